@@ -63,6 +63,11 @@ def _lib(omp: bool = False):
         L.orc_power_lmax.argtypes = [ctypes.c_int, P, ctypes.c_int]
         L.orc_jacobi_lmax.restype = ctypes.c_double
         L.orc_jacobi_lmax.argtypes = [ctypes.c_int, P]
+        L.orc_row_update.restype = ctypes.c_int64
+        L.orc_row_update.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int, P, ctypes.c_int64, P, P,
+                                     ctypes.c_int64, ctypes.c_double, ctypes.c_uint64,
+                                     ctypes.c_uint64, ctypes.c_int, P, P, P, P, P, P, P, P, P]
         L.orc_create.restype = P
         L.orc_create.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_double]
         L.orc_destroy.argtypes = [P]
@@ -145,6 +150,27 @@ def jacobi_lmax(H: np.ndarray) -> float:
     """Exact max eig(H) by cyclic Jacobi rotations."""
     H = np.ascontiguousarray(H, dtype=np.float64)
     return float(_lib().orc_jacobi_lmax(H.shape[0], _ptr(H)))
+
+
+def row_update(mode: int, lam: float, factors, idx: np.ndarray, vals: np.ndarray, q0: int,
+               c: float, seed: int, ao_iter: int, inner: int, y: np.ndarray, a: np.ndarray,
+               power_iters: int = 10, lp_exact: bool = False) -> dict:
+    """Alg. 1 lines 5-13 for one row given its observations in bucket order."""
+    L = _lib()
+    fac = [np.ascontiguousarray(f, dtype=np.float64) for f in factors]
+    order, R = len(fac), fac[0].shape[1]
+    arr = (ctypes.c_void_p * order)(*[f.ctypes.data for f in fac])
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    a_out, y_out, H, g = np.zeros(R), np.zeros(R), np.zeros((R, R)), np.zeros(R)
+    Lp, Lx, beta = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    k = L.orc_row_update(order, mode, R, lam, power_iters, int(lp_exact), ctypes.cast(arr, ctypes.c_void_p),
+                         vals.shape[0], _ptr(idx), _ptr(vals), q0, c, seed, ao_iter, inner, _ptr(y),
+                         _ptr(a), _ptr(a_out), _ptr(y_out), _ptr(H), _ptr(g), ctypes.byref(Lp),
+                         ctypes.byref(Lx), ctypes.byref(beta))
+    return dict(k=int(k), a=a_out, y=y_out, H=H, grad=g, L=Lp.value, L_exact=Lx.value, beta=beta.value)
 
 
 class Oracle:

@@ -332,21 +332,103 @@ int orc_init_factors(orc_state* s, uint64_t init_seed) {
 uint64_t orc_get_ao_iter(const orc_state* s) { return s->ao_iter; }
 void orc_set_ao_iter(orc_state* s, uint64_t k) { s->ao_iter = k; }
 
-/* Algorithm 1, S_NMC(X_(i), M_(i), K_k^(i), U_k^(i), lambda), with the
- * Khatri-Rao product K_k^(i) never formed: the row of K for an observed
- * entry is the Hadamard product of the other factors' rows at that entry's
- * indices (Sec. II, unfolding eq.; Sec. III, K definition), read from the
- * current factors, so modes already visited in this AO iteration contribute
- * their updated values. */
+/* Alg. 1 lines 5-13 for one row p of the mode-`mode` unfolding.  The row's
+ * observations are given explicitly in bucket order: idx[n][order], vals[n],
+ * the first at bucket position q0.  The row of K_k^(i) for an observation is
+ * the Hadamard product of the other factors' rows at its indices (Sec. II,
+ * unfolding eq.; Sec. III, K definition); it is never formed as a matrix.
+ * y = Y_l(p,:), a = A_l(p,:) on input; a_out = A_{l+1}(p,:), y_out =
+ * Y_{l+1}(p,:) on output (unchanged copies when the row is skipped).
+ * Optional outputs (may be NULL): H[R*R], grad[R], L (used), L_exact, beta.
+ * Returns k = B_{l,p}, or -1 when L_p <= 0 made the row skip. */
+int64_t orc_row_update(int order, int mode, int rank, double lambda, int power_iters, int lp_exact,
+                       const double* const* U, int64_t n, const int32_t* idx, const double* vals,
+                       int64_t q0, double c, uint64_t seed, uint64_t ao_iter, int inner,
+                       const double* y, const double* a, double* a_out, double* y_out,
+                       double* H_out, double* grad_out, double* L_out, double* Lx_out,
+                       double* beta_out) {
+    const int N = order, R = rank;
+    const double lam = lambda;
+    for (int r = 0; r < R; ++r) {
+        a_out[r] = a[r];
+        y_out[r] = y[r];
+    }
+    const int64_t k = orc_sample_count(c, n);
+    if (k == 0) return 0;                          /* B_{l,p} = 0: skip the row */
+    int64_t* sel = (int64_t*)malloc(sizeof(int64_t) * (size_t)k);
+    double* W = (double*)calloc((size_t)R, sizeof(double));
+    double* Z = (double*)calloc((size_t)R, sizeof(double));
+    double* G = (double*)calloc((size_t)R, sizeof(double));
+    double* H = (double*)calloc((size_t)R * R, sizeof(double));
+    double* kr = (double*)malloc(sizeof(double) * (size_t)R);
+
+    /* line 5: M_hat_l(p,:) = sample(M(p,:)) */
+    orc_sample_row(seed, (uint32_t)mode, ao_iter, (uint32_t)inner, q0, n, k, sel);
+
+    for (int64_t t = 0; t < k; ++t) {
+        const int64_t j = sel[t] - q0;
+        const int32_t* ix = idx + j * N;
+        const double x = vals[j];
+        /* row of B = K_k^(i) at this observation's column */
+        for (int r = 0; r < R; ++r) kr[r] = 1.0;
+        for (int m = 0; m < N; ++m) {
+            if (m == mode) continue;
+            const double* u = U[m] + (int64_t)ix[m] * R;
+            for (int r = 0; r < R; ++r) kr[r] *= u[r];
+        }
+        /* line 6: W_l(p,:) = -(M_hat(p,:) .* X(p,:)) B */
+        for (int r = 0; r < R; ++r) W[r] -= x * kr[r];
+        /* line 7: Z_l(p,:) = (M_hat(p,:) .* (Y_l(p,:) B^T)) B */
+        double yb = 0.0;
+        for (int r = 0; r < R; ++r) yb += y[r] * kr[r];
+        for (int r = 0; r < R; ++r) Z[r] += yb * kr[r];
+        /* line 9: H_{l,p} = B^T diag(M_hat(p,:)) B + lambda I */
+        for (int r = 0; r < R; ++r)
+            for (int q = 0; q < R; ++q) H[r * R + q] += kr[r] * kr[q];
+    }
+    for (int r = 0; r < R; ++r) H[r * R + r] += lam;
+    /* line 8: gradient = W + Z + lambda Y_l(p,:) */
+    for (int r = 0; r < R; ++r) G[r] = W[r] + Z[r] + lam * y[r];
+    /* line 10: L_p = max(eig(H_{l,p})) */
+    const double Lpm = orc_power_lmax(R, H, power_iters);
+    const double L = lp_exact ? orc_jacobi_lmax(R, H) : Lpm;
+    if (H_out) memcpy(H_out, H, sizeof(double) * (size_t)R * R);
+    if (grad_out) memcpy(grad_out, G, sizeof(double) * (size_t)R);
+    if (L_out) *L_out = L;
+    if (Lx_out) *Lx_out = orc_jacobi_lmax(R, H);
+    int64_t ret = k;
+    if (L > 0.0) {
+        /* line 11: A_{l+1}(p,:) = (Y_l(p,:) - grad / L_p)_+ */
+        /* line 12: beta = (sqrt(L_p) - sqrt(lambda)) / (sqrt(L_p) + sqrt(lambda)) */
+        const double beta = (sqrt(L) - sqrt(lam)) / (sqrt(L) + sqrt(lam));
+        for (int r = 0; r < R; ++r) {
+            double anew = y[r] - G[r] / L;
+            if (!(anew > 0.0)) anew = 0.0;
+            /* line 13: Y_{l+1} = A_{l+1} + beta (A_{l+1} - A_l) */
+            a_out[r] = anew;
+            y_out[r] = anew + beta * (anew - a[r]);
+        }
+        if (beta_out) *beta_out = beta;
+    } else {
+        ret = -1;                                  /* L_p <= 0: skip as well */
+    }
+    free(sel); free(W); free(Z); free(G); free(H); free(kr);
+    return ret;
+}
+
+/* Algorithm 1, S_NMC(X_(i), M_(i), K_k^(i), U_k^(i), lambda): MAX_INNER
+ * passes of the row update over every row (Alg. 3: rows in parallel), with
+ * the factors of the other modes as they are now, so that modes already
+ * visited in this AO iteration contribute their updated values. */
 int orc_snmc(orc_state* s, int mode, double c, uint64_t seed) {
     if (mode < 0 || mode >= s->order || !(c > 0.0) || c > 1.0) return -1;
     if (!s->row_ptr[0]) return -1;
     const int N = s->order, R = s->rank;
     const int64_t P = s->dims[mode];
-    const double lam = s->lambda;
     double* A = s->U[mode];                      /* A_l, updated in place */
     double* Y = (double*)malloc(sizeof(double) * (size_t)P * (size_t)R);
     memcpy(Y, A, sizeof(double) * (size_t)P * (size_t)R); /* Y_0 = A_0 = A_* */
+    const double* const* U = (const double* const*)s->U;
 
     if (s->debug) {
         orc_free_debug(s);
@@ -367,75 +449,30 @@ int orc_snmc(orc_state* s, int mode, double c, uint64_t seed) {
         for (int64_t p = 0; p < P; ++p) {          /* for p = 1..P (Alg. 3: in parallel) */
             const int64_t q0 = s->row_ptr[mode][p];
             const int64_t n = s->row_ptr[mode][p + 1] - q0;
-            const int64_t k = orc_sample_count(c, n);
-            if (k == 0) {                           /* B_{l,p} = 0: skip the row */
-                if (l == 0) skipped += 1;
-                continue;
+            int32_t* ridx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n * N + 1));
+            double* rval = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+            for (int64_t j = 0; j < n; ++j) {
+                const int64_t e = s->perm[mode][q0 + j];
+                memcpy(ridx + j * N, s->idx + e * N, sizeof(int32_t) * (size_t)N);
+                rval[j] = s->vals[e];
             }
-            int64_t* sel = (int64_t*)malloc(sizeof(int64_t) * (size_t)k);
-            double* W = (double*)calloc((size_t)R, sizeof(double));
-            double* Z = (double*)calloc((size_t)R, sizeof(double));
-            double* G = (double*)calloc((size_t)R, sizeof(double));
-            double* H = (double*)calloc((size_t)R * R, sizeof(double));
-            double* kr = (double*)malloc(sizeof(double) * (size_t)R);
-            double* y = Y + p * R;
             double* a = A + p * R;
-
-            /* line 5: M_hat_l(p,:) = sample(M(p,:)) */
-            orc_sample_row(seed, (uint32_t)mode, s->ao_iter, (uint32_t)l, q0, n, k, sel);
-            visits += k;
-
-            for (int64_t t = 0; t < k; ++t) {
-                const int64_t e = s->perm[mode][sel[t]];
-                const int32_t* ix = s->idx + e * N;
-                const double x = s->vals[e];
-                /* row of B = K_k^(i) at this entry's column */
-                for (int r = 0; r < R; ++r) kr[r] = 1.0;
-                for (int j = 0; j < N; ++j) {
-                    if (j == mode) continue;
-                    const double* u = s->U[j] + (int64_t)ix[j] * R;
-                    for (int r = 0; r < R; ++r) kr[r] *= u[r];
-                }
-                /* line 6: W_l(p,:) = -(M_hat(p,:) .* X(p,:)) B */
-                for (int r = 0; r < R; ++r) W[r] -= x * kr[r];
-                /* line 7: Z_l(p,:) = (M_hat(p,:) .* (Y_l(p,:) B^T)) B */
-                double yb = 0.0;
-                for (int r = 0; r < R; ++r) yb += y[r] * kr[r];
-                for (int r = 0; r < R; ++r) Z[r] += yb * kr[r];
-                /* line 9: H_{l,p} = B^T diag(M_hat(p,:)) B + lambda I */
-                for (int r = 0; r < R; ++r)
-                    for (int q = 0; q < R; ++q) H[r * R + q] += kr[r] * kr[q];
-            }
-            for (int r = 0; r < R; ++r) H[r * R + r] += lam;
-            /* line 8: gradient = W + Z + lambda Y_l(p,:) */
-            for (int r = 0; r < R; ++r) G[r] = W[r] + Z[r] + lam * y[r];
-            /* line 10: L_p = max(eig(H_{l,p})) */
-            double Lpm = orc_power_lmax(R, H, s->power_iters);
-            double L = s->lp_exact ? orc_jacobi_lmax(R, H) : Lpm;
-            if (s->debug && l == s->max_inner - 1) {
-                memcpy(s->dbg_H + p * R * R, H, sizeof(double) * (size_t)R * R);
-                memcpy(s->dbg_grad + p * R, G, sizeof(double) * (size_t)R);
-                s->dbg_L[p] = L;
-                s->dbg_Lx[p] = orc_jacobi_lmax(R, H);
-                s->dbg_kp[p] = k;
-            }
-            if (L > 0.0) {
-                /* line 11: A_{l+1}(p,:) = (Y_l(p,:) - grad / L_p)_+ */
-                /* line 12: beta = (sqrt(L_p) - sqrt(lambda)) / (sqrt(L_p) + sqrt(lambda)) */
-                double beta = (sqrt(L) - sqrt(lam)) / (sqrt(L) + sqrt(lam));
-                for (int r = 0; r < R; ++r) {
-                    double anew = y[r] - G[r] / L;
-                    if (!(anew > 0.0)) anew = 0.0;
-                    /* line 13: Y_{l+1} = A_{l+1} + beta (A_{l+1} - A_l) */
-                    double ynew = anew + beta * (anew - a[r]);
-                    a[r] = anew;
-                    y[r] = ynew;
-                }
-                if (s->debug && l == s->max_inner - 1) s->dbg_beta[p] = beta;
-            } else if (l == 0) {
-                skipped += 1;                       /* L_p <= 0: skip as well */
-            }
-            free(sel); free(W); free(Z); free(G); free(H); free(kr);
+            double* y = Y + p * R;
+            double* anew = (double*)malloc(sizeof(double) * (size_t)R);
+            double* ynew = (double*)malloc(sizeof(double) * (size_t)R);
+            const int dbg = s->debug && l == s->max_inner - 1;
+            const int64_t k = orc_row_update(N, mode, R, s->lambda, s->power_iters, s->lp_exact, U, n,
+                                             ridx, rval, q0, c, seed, s->ao_iter, l, y, a, anew, ynew,
+                                             dbg ? s->dbg_H + p * R * R : NULL,
+                                             dbg ? s->dbg_grad + p * R : NULL,
+                                             dbg ? s->dbg_L + p : NULL, dbg ? s->dbg_Lx + p : NULL,
+                                             dbg ? s->dbg_beta + p : NULL);
+            if (dbg) s->dbg_kp[p] = k > 0 ? k : orc_sample_count(c, n);
+            if (k <= 0 && l == 0) skipped += 1;
+            if (k != 0) visits += k > 0 ? k : orc_sample_count(c, n);
+            memcpy(a, anew, sizeof(double) * (size_t)R);
+            memcpy(y, ynew, sizeof(double) * (size_t)R);
+            free(ridx); free(rval); free(anew); free(ynew);
         }
     }
     free(Y);

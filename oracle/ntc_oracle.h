@@ -68,6 +68,18 @@ double orc_power_lmax(int R, const double* H, int iters);
 /* Largest eigenvalue of a symmetric matrix by cyclic Jacobi rotations. */
 double orc_jacobi_lmax(int R, const double* H);
 
+/* Alg. 1 lines 5-13 for one row, with the row's observations given in bucket
+ * order (idx[n][order], vals[n]; the first at bucket position q0) and all
+ * factors U[order] ([dims][rank] row-major).  y/a: Y_l(p,:), A_l(p,:); outputs
+ * A_{l+1}(p,:), Y_{l+1}(p,:) and optionally H, gradient, L, exact L, beta.
+ * Returns B_{l,p} (0 when skipped), or -1 when L_p <= 0 skipped the row. */
+int64_t orc_row_update(int order, int mode, int rank, double lambda, int power_iters, int lp_exact,
+                       const double* const* U, int64_t n, const int32_t* idx, const double* vals,
+                       int64_t q0, double c, uint64_t seed, uint64_t ao_iter, int inner,
+                       const double* y, const double* a, double* a_out, double* y_out,
+                       double* H_out, double* grad_out, double* L_out, double* Lx_out,
+                       double* beta_out);
+
 /* ---- whole-problem state (Algorithms 1-2) ---- */
 typedef struct orc_state orc_state;
 

@@ -1,0 +1,289 @@
+// aux_kernels.cuh -- device kernels around the NMC update: per-mode bucketing
+// of the observed entries by row (a stable LSD radix counting sort), index
+// validation, initial factors, and the model evaluations (eq. 1) behind
+// predict, RMSE and the cost of eq. 3.
+#pragma once
+
+#include "ntc_internal.cuh"
+
+namespace ntc {
+
+constexpr int kSortIPT = 16;                       // keys per thread per tile
+constexpr int kSortTile = kThreads * kSortIPT;     // 4096 keys per tile
+
+// Any index outside [0, dims[i]) sets *bad.
+__global__ void k_validate(const int32_t* idx, int64_t n, int order, const int64_t* dims_dev,
+                           unsigned* bad) {
+    int64_t dims[kMaxOrder];
+    for (int i = 0; i < order; ++i) dims[i] = dims_dev[i];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        for (int i = 0; i < order; ++i) {
+            const int32_t v = idx[e * order + i];
+            if (v < 0 || v >= dims[i]) atomicOr(bad, 1u);
+        }
+    }
+}
+
+__global__ void k_extract_keys(const int32_t* idx, int64_t n, int order, int mode, uint32_t* keys,
+                               uint32_t* payload) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        keys[e] = (uint32_t)idx[e * order + mode];
+        payload[e] = (uint32_t)e;
+    }
+}
+
+// Per-tile digit histograms, digit-major: hist[d * ntiles + tile].
+__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* keys, int64_t n, int shift,
+                                                         uint32_t* hist, int ntiles) {
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int r = 0; r < kSortIPT; ++r) {
+        const int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: warp w of a tile owns keys [w*512, w*512+512) in order, in
+// 16 rounds of 32; equal digits within a round are ranked by lane, rounds and
+// warps in order, so the output keeps the input order of equal keys.
+__global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* kin, const uint32_t* vin,
+                                                            uint32_t* kout, uint32_t* vout, int64_t n,
+                                                            int shift, const uint32_t* offs, int ntiles) {
+    __shared__ unsigned wh[kThreads / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortIPT);
+    uint32_t key[kSortIPT], val[kSortIPT];
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        key[r] = i < n ? kin[i] : 0u;
+        val[r] = i < n ? vin[i] : 0u;
+    }
+    for (int d = lane; d < 256; d += 32) wh[warp][d] = 0;
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        const bool valid = base + r * 32 + lane < n;
+        const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & lt) == 0) wh[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        unsigned run = offs[(int64_t)d * ntiles + blockIdx.x];
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const unsigned t = wh[w][d];
+            wh[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        const bool valid = base + r * 32 + lane < n;
+        const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned pos = 0;
+        if (valid) pos = wh[warp][d] + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wh[warp][d] += __popc(peers);
+        __syncwarp();
+        if (valid) {
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+// Exclusive scan of n uint32 values (n < 2^31), three phases: block sums,
+// a one-block scan of the block sums, block-local scans with carry-in.
+constexpr int kScanBlock = 2048;
+
+__global__ void __launch_bounds__(kThreads) k_scan_sums(const uint32_t* in, int64_t n, uint32_t* sums) {
+    __shared__ int tmp[kThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    unsigned s = 0;
+    for (int i = threadIdx.x; i < kScanBlock; i += kThreads)
+        if (base + i < n) s += in[base + i];
+    int tot;
+    block_exclusive_scan((int)s, tmp, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = (uint32_t)tot;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_top(uint32_t* sums, int nb) {
+    __shared__ int tmp[kThreads / 32 + 1];
+    unsigned carry = 0;
+    for (int base = 0; base < nb; base += kThreads) {
+        const int i = base + threadIdx.x;
+        const unsigned v = i < nb ? sums[i] : 0u;
+        int tot;
+        const int ex = block_exclusive_scan((int)v, tmp, &tot);
+        if (i < nb) sums[i] = carry + (unsigned)ex;
+        carry += (unsigned)tot;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_apply(const uint32_t* in, int64_t n, const uint32_t* sums,
+                                                         uint32_t* out) {
+    __shared__ int tmp[kThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    constexpr int PER = kScanBlock / kThreads;   // 8 consecutive values per thread
+    unsigned v[PER];
+    unsigned s = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int64_t i = base + (int64_t)threadIdx.x * PER + j;
+        v[j] = i < n ? in[i] : 0u;
+        s += v[j];
+    }
+    int tot;
+    unsigned run = sums[blockIdx.x] + (unsigned)block_exclusive_scan((int)s, tmp, &tot);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int64_t i = base + (int64_t)threadIdx.x * PER + j;
+        if (i < n) out[i] = run;
+        run += v[j];
+    }
+}
+
+// row_ptr from sorted row keys: row_ptr[r] = first position whose key >= r.
+__global__ void k_row_ptr(const uint32_t* keys, int64_t n, int64_t dim, int64_t* row_ptr) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q <= n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = q == 0 ? 0 : (int64_t)keys[q - 1] + 1;
+        const int64_t hi = q == n ? dim : (int64_t)keys[q];
+        for (int64_t r = lo; r <= hi; ++r) row_ptr[r] = q;
+    }
+}
+
+// Bucket entries of `mode` in sorted order: other modes' indices, then value.
+template <int EW>
+__global__ void k_fill_bucket(const int32_t* idx, const float* vals, const uint32_t* perm, int64_t n,
+                              int order, int mode, Entry<EW>* out) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = perm[q];
+        Entry<EW> en;
+#pragma unroll
+        for (int w = 0; w < EW; ++w) en.w[w] = 0;
+        int o = 0;
+        for (int i = 0; i < order; ++i)
+            if (i != mode) en.w[o++] = idx[e * order + i];
+        en.w[EW - 1] = __float_as_int(vals[e]);
+        out[q] = en;
+    }
+}
+
+// Fixed-order double-precision sums: per-block partials, then one block.
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kThreads / 32; ++w) t += sh[w];
+    __syncthreads();
+    return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kThreads) k_sum_f32(const float* x, int64_t n, double* partial) {
+    __shared__ double sh[kThreads / 32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        s += (double)x[i];
+    const double t = block_sum_d(s, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sum_partials(const double* partial, int nb, double* out) {
+    __shared__ double sh[kThreads / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += kThreads) s += partial[i];
+    const double t = block_sum_d(s, sh);
+    if (threadIdx.x == 0) *out = t;
+}
+
+// Initial factors: i.i.d. U[0, 2a] from Philox(counter {0xFFFF, mode, row,
+// col}, key init_seed), u = (word0 + 1/2) 2^-32, drawn in double, stored
+// rounded to float; padding columns are zero.
+__global__ void k_init_factor(float* U, uint16_t* Ub, int64_t rows, int R, int rp, int mode,
+                              const double* sum_vals, int64_t nnz, int order, uint32_t k0, uint32_t k1) {
+    const double mean = nnz > 0 ? *sum_vals / (double)nnz : 0.0;
+    const double a = mean > 0.0 ? pow(mean / (double)R, 1.0 / (double)order) : 0.0;
+    const int64_t total = rows * rp;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / rp;
+        const int r = (int)(t - p * rp);
+        float v = 0.f;
+        if (r < R) {
+            const uint4 w = philox4(0xFFFFu, (uint32_t)mode, (uint32_t)p, (uint32_t)r, k0, k1);
+            const double u = ((double)w.x + 0.5) * (1.0 / 4294967296.0);
+            v = (float)(2.0 * a * u);
+        }
+        U[t] = v;
+        if (Ub) Ub[t] = f32_to_bf16_rne(v);
+    }
+}
+
+__global__ void k_to_bf16(const float* U, uint16_t* Ub, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        Ub[t] = f32_to_bf16_rne(U[t]);
+}
+
+struct FactorSet {
+    const float* U[kMaxOrder];
+    int order, R, rp;
+};
+
+// Model value (eq. 1) at one index, float32 products and sum.
+__device__ __forceinline__ float model_at(const FactorSet& f, const int32_t* ix) {
+    float acc = 0.f;
+    for (int r = 0; r < f.R; ++r) {
+        float p = f.U[0][(size_t)ix[0] * f.rp + r];
+        for (int i = 1; i < f.order; ++i) p *= f.U[i][(size_t)ix[i] * f.rp + r];
+        acc += p;
+    }
+    return acc;
+}
+
+__global__ void k_predict(FactorSet f, const int32_t* idx, int64_t n, float* out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = model_at(f, idx + e * f.order);
+}
+
+// Per-block double sums of (x - model)^2.
+__global__ void __launch_bounds__(kThreads) k_sq_resid(FactorSet f, const int32_t* idx, const float* vals,
+                                                       int64_t n, double* partial) {
+    __shared__ double sh[kThreads / 32];
+    double s = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
+        const double d = (double)vals[e] - (double)model_at(f, idx + e * f.order);
+        s += d * d;
+    }
+    const double t = block_sum_d(s, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sq_sum(const float* x, int64_t n, double* partial) {
+    __shared__ double sh[kThreads / 32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        s += (double)x[i] * (double)x[i];
+    const double t = block_sum_d(s, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+}  // namespace ntc

@@ -1,0 +1,833 @@
+// ntc_api.cu -- host orchestrator and C ABI (include/ntc.h) of the GB300
+// library for AO accelerated stochastic nonnegative tensor completion
+// (arXiv 2109.09534).  The handle owns device memory, buckets the observed
+// entries, plans the per-mode row work (light rows: one block each; heavy
+// rows: split into chunks) and enqueues Algorithm 2 around Algorithm 1 on one
+// CUDA stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ntc.h"
+#include "aux_kernels.cuh"
+#include "nmc_kernels.cuh"
+
+using namespace ntc;
+
+namespace {
+
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    ~DevMem() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // grow-only; contents are not preserved
+    cudaError_t ensure(size_t b) {
+        if (b <= bytes && p) return cudaSuccess;
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = b;
+        return cudaSuccess;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct ModePlan {
+    bool valid = false;
+    double c = 0.0;
+    int heavy_threshold = 0, chunk = 0;
+    double bracket_z = 0.0;
+    int64_t visits = 0, visits_heavy = 0, rows_updated = 0, rows_skipped = 0;
+    int n_light = 0, n_heavy = 0, n_chunks = 0;
+    int64_t cand_total = 0, extra_total = 0;
+    DevMem light_rows, light_k, chunks, chunk_caps, heavy, bracket, heavy_cand;
+};
+
+int pad_rank(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
+
+}  // namespace
+
+struct ntc_handle {
+    int order = 0;
+    int64_t dims[kMaxOrder] = {};
+    int rank = 0, rp = 0;
+    double lambda = 0.0;
+    // parameters
+    int max_inner = 1, power_iters = 10, storage_bf16 = 0, keep_perm = 0;
+    uint64_t init_seed = 3;
+    double bracket_z = 7.0;
+    int heavy_threshold = 4096, chunk = 16384;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    // state
+    uint64_t ao_iter = 0;
+    int64_t nnz = -1;
+    bool factor_set[kMaxOrder] = {};
+    std::string err;
+    ntc_stats stats = {};
+    // device data
+    DevMem U[kMaxOrder], Ub[kMaxOrder], Y;
+    DevMem row_ptr[kMaxOrder], bucket[kMaxOrder], perm[kMaxOrder];
+    DevMem coo_idx, coo_val, dims_dev;
+    std::vector<int64_t> row_ptr_h[kMaxOrder];
+    ModePlan plan[kMaxOrder];
+    // scratch
+    DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, stat, red, mask;
+};
+
+namespace {
+
+ntc_status fail(ntc_handle* h, ntc_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+#define NTC_CUDA(h, call)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? NTC_ERR_OOM : NTC_ERR_CUDA,  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                \
+        }                                                                                   \
+    } while (0)
+
+int ew_of(int order) { return order <= 4 ? 4 : 8; }
+
+int grid_for(int64_t n, int per_block = 256, int cap = 152 * 16) {
+    int64_t g = (n + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// ---- one-time smem attributes per kernel instantiation --------------------
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---- mode update launches ---------------------------------------------------
+template <int RP, int EW, bool BF>
+cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, cudaStream_t s, bool mask_only,
+                          int64_t* launches) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e;
+        if ((e = set_smem(k_light<RP, EW, BF>, LightSmem<RP, EW, BF>::BYTES)) != cudaSuccess) return e;
+        if ((e = set_smem(k_heavy_gram<RP, EW, BF>, heavy_gram_smem<RP, EW, BF>())) != cudaSuccess) return e;
+        if ((e = set_smem(k_heavy_finish<RP>, heavy_finish_smem<RP>())) != cudaSuccess) return e;
+        attr = true;
+    }
+    if (p.n_light > 0) {
+        k_light<RP, EW, BF><<<p.n_light, kThreads, LightSmem<RP, EW, BF>::BYTES, s>>>(a);
+        ++*launches;
+    }
+    if (p.n_heavy > 0) {
+        cudaError_t e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
+        if (e != cudaSuccess) return e;
+        k_heavy_sample<<<p.n_chunks, kThreads, 0, s>>>(a);
+        k_heavy_resolve<<<p.n_heavy, kThreads, 0, s>>>(a);
+        *launches += 2;
+        if (mask_only) {
+            k_heavy_mask<<<p.n_chunks + p.n_heavy, kThreads, 0, s>>>(a);
+            ++*launches;
+        } else {
+            k_heavy_gram<RP, EW, BF><<<p.n_chunks + p.n_heavy, kThreads, heavy_gram_smem<RP, EW, BF>(), s>>>(a);
+            k_heavy_finish<RP><<<p.n_heavy, kThreads, heavy_finish_smem<RP>(), s>>>(a);
+            *launches += 2;
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <int RP>
+cudaError_t launch_mode_rp(int ew, bool bf, const ModeArgs& a, const ModePlan& p, cudaStream_t s, bool mo,
+                           int64_t* l) {
+    if (ew == 4) return bf ? launch_mode_t<RP, 4, true>(a, p, s, mo, l) : launch_mode_t<RP, 4, false>(a, p, s, mo, l);
+    return bf ? launch_mode_t<RP, 8, true>(a, p, s, mo, l) : launch_mode_t<RP, 8, false>(a, p, s, mo, l);
+}
+
+cudaError_t launch_mode(int rp, int ew, bool bf, const ModeArgs& a, const ModePlan& p, cudaStream_t s, bool mo,
+                        int64_t* l) {
+    switch (rp) {
+        case 8: return launch_mode_rp<8>(ew, bf, a, p, s, mo, l);
+        case 16: return launch_mode_rp<16>(ew, bf, a, p, s, mo, l);
+        case 32: return launch_mode_rp<32>(ew, bf, a, p, s, mo, l);
+        default: return launch_mode_rp<64>(ew, bf, a, p, s, mo, l);
+    }
+}
+
+int partial_width(int rp) {
+    const int T = rp / 8;
+    return T * (T + 1) / 2 * 72;
+}
+
+// ---- per-(mode, c) plan ------------------------------------------------------
+ntc_status build_plan(ntc_handle* h, int mode, double c) {
+    ModePlan& p = h->plan[mode];
+    if (p.valid && p.c == c && p.heavy_threshold == h->heavy_threshold && p.chunk == h->chunk &&
+        p.bracket_z == h->bracket_z)
+        return NTC_OK;
+    p.valid = false;
+    const std::vector<int64_t>& rp = h->row_ptr_h[mode];
+    const int64_t P = h->dims[mode];
+    std::vector<std::pair<int64_t, int32_t>> light;   // (n, row)
+    std::vector<int32_t> light_k;
+    std::vector<int4> chunks, caps, heavy, hcand;
+    std::vector<longlong2> brk;
+    int64_t visits = 0, visits_heavy = 0, updated = 0, skipped = 0, cand_total = 0, extra_total = 0;
+    for (int64_t r = 0; r < P; ++r) {
+        const int64_t n = rp[r + 1] - rp[r];
+        const int64_t k = (int64_t)std::floor(c * (double)n);   // B_{l,p} = floor(c ||M(p,:)||_0)
+        if (k == 0) {
+            ++skipped;
+            continue;
+        }
+        ++updated;
+        visits += k;
+        if (n <= h->heavy_threshold) {
+            light.push_back({n, (int32_t)r});
+            continue;
+        }
+        visits_heavy += k;
+        const int hidx = (int)heavy.size();
+        const int64_t nch = (n + h->chunk - 1) / h->chunk;
+        long long lo, hi;
+        if (k == n) {
+            lo = hi = 1ll << 32;
+        } else {
+            const double q = (double)k / (double)n;
+            const double sd = std::sqrt(q * (1.0 - q) / (double)n);
+            const double delta = h->bracket_z * sd;
+            const double two32 = 4294967296.0;
+            double l = std::max(0.0, q - delta) * two32, u = std::min(1.0, q + delta) * two32;
+            lo = (long long)std::floor(l);
+            hi = (long long)std::ceil(u);
+            if (h->bracket_z <= 0.0) lo = hi = (long long)std::floor(q * two32);
+            lo = std::max(0ll, std::min(lo, 1ll << 32));
+            hi = std::max(lo, std::min(hi, 1ll << 32));
+        }
+        const int cb = (int)chunks.size();
+        const int64_t cbeg = cand_total;
+        for (int64_t j = 0; j < nch; ++j) {
+            const int64_t pb = rp[r] + (j * n) / nch, pe = rp[r] + ((j + 1) * n) / nch;
+            const double expect = (double)(pe - pb) * (double)(hi - lo) / 4294967296.0;
+            int cap = hi > lo ? (int)std::ceil(expect + 8.0 * std::sqrt(expect) + 8.0) : 0;
+            cap = (cap + 3) & ~3;
+            chunks.push_back(make_int4(hidx, (int)pb, (int)pe, (int)cand_total));
+            caps.push_back(make_int4(cap, 0, 0, 0));
+            cand_total += cap;
+        }
+        heavy.push_back(make_int4((int)r, (int)k, cb, (int)chunks.size()));
+        brk.push_back(make_longlong2(lo, hi));
+        const int ccap = (int)(cand_total - cbeg);
+        hcand.push_back(make_int4((int)cbeg, ccap, (int)extra_total, ccap));
+        extra_total += ccap;
+    }
+    // longest light rows first: better tail behaviour, same results
+    std::stable_sort(light.begin(), light.end(),
+                     [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) {
+                         return x.first > y.first;
+                     });
+    std::vector<int32_t> lrows(light.size());
+    light_k.resize(light.size());
+    for (size_t i = 0; i < light.size(); ++i) {
+        lrows[i] = light[i].second;
+        light_k[i] = (int32_t)std::floor(c * (double)light[i].first);
+    }
+    if (cand_total >= (1ll << 31) || extra_total >= (1ll << 31))
+        return fail(h, NTC_ERR_ARG, "sampler bracket too wide for this row size");
+    auto up = [&](DevMem& m, const void* src, size_t bytes) -> cudaError_t {
+        cudaError_t e = m.ensure(bytes);
+        if (e != cudaSuccess || bytes == 0) return e;
+        return cudaMemcpyAsync(m.p, src, bytes, cudaMemcpyHostToDevice, h->stream);
+    };
+    NTC_CUDA(h, up(p.light_rows, lrows.data(), lrows.size() * 4));
+    NTC_CUDA(h, up(p.light_k, light_k.data(), light_k.size() * 4));
+    NTC_CUDA(h, up(p.chunks, chunks.data(), chunks.size() * sizeof(int4)));
+    NTC_CUDA(h, up(p.chunk_caps, caps.data(), caps.size() * sizeof(int4)));
+    NTC_CUDA(h, up(p.heavy, heavy.data(), heavy.size() * sizeof(int4)));
+    NTC_CUDA(h, up(p.bracket, brk.data(), brk.size() * sizeof(longlong2)));
+    NTC_CUDA(h, up(p.heavy_cand, hcand.data(), hcand.size() * sizeof(int4)));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));   // host vectors go out of scope
+    p.c = c;
+    p.heavy_threshold = h->heavy_threshold;
+    p.chunk = h->chunk;
+    p.bracket_z = h->bracket_z;
+    p.visits = visits;
+    p.visits_heavy = visits_heavy;
+    p.rows_updated = updated;
+    p.rows_skipped = skipped;
+    p.n_light = (int)light.size();
+    p.n_heavy = (int)heavy.size();
+    p.n_chunks = (int)chunks.size();
+    p.cand_total = cand_total;
+    p.extra_total = extra_total;
+    // scratch sized for this plan
+    NTC_CUDA(h, h->vis.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(h->nnz, 1)));
+    NTC_CUDA(h, h->vis_cnt.ensure(sizeof(uint32_t) * (size_t)std::max(p.n_chunks, 1)));
+    NTC_CUDA(h, h->cand_cnt.ensure(sizeof(uint32_t) * (size_t)std::max(p.n_chunks, 1)));
+    NTC_CUDA(h, h->cand.ensure(sizeof(unsigned long long) * (size_t)std::max<int64_t>(cand_total, 1)));
+    NTC_CUDA(h, h->extra.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(extra_total, 1)));
+    NTC_CUDA(h, h->extra_cnt.ensure(sizeof(uint32_t) * (size_t)std::max(p.n_heavy, 1)));
+    NTC_CUDA(h, h->flags.ensure(sizeof(uint32_t) * (size_t)std::max(p.n_heavy, 1)));
+    NTC_CUDA(h, h->partial.ensure(sizeof(float) * (size_t)partial_width(h->rp) *
+                                  (size_t)std::max(p.n_chunks + p.n_heavy, 1)));
+    p.valid = true;
+    return NTC_OK;
+}
+
+ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t ao_iter) {
+    ModeArgs a;
+    memset(&a, 0, sizeof(a));
+    const ModePlan& p = h->plan[mode];
+    int o = 0;
+    for (int i = 0; i < h->order; ++i) {
+        if (i == mode) continue;
+        a.other[o++] = h->storage_bf16 ? (const void*)h->Ub[i].p : (const void*)h->U[i].p;
+    }
+    a.n_other = h->order - 1;
+    a.rank = h->rank;
+    a.rp = h->rp;
+    a.lambda = (float)h->lambda;
+    a.lambda_d = h->lambda;
+    a.power_iters = h->power_iters;
+    a.U = h->U[mode].as<float>();
+    a.Ub = h->storage_bf16 ? h->Ub[mode].as<uint16_t>() : nullptr;
+    a.Y = h->max_inner > 1 ? h->Y.as<float>() : nullptr;
+    a.read_y = inner > 0 ? 1 : 0;
+    a.write_y = inner + 1 < h->max_inner ? 1 : 0;
+    a.row_ptr = h->row_ptr[mode].as<int64_t>();
+    a.bucket = h->bucket[mode].p;
+    a.ss.mode = (uint32_t)mode;
+    a.ss.iter = (uint32_t)ao_iter;
+    a.ss.inner = (uint32_t)inner;
+    a.ss.k0 = (uint32_t)seed;
+    a.ss.k1 = (uint32_t)(seed >> 32);
+    a.light_rows = p.light_rows.as<int32_t>();
+    a.light_k = p.light_k.as<int32_t>();
+    a.chunks = p.chunks.as<int4>();
+    a.chunk_caps = p.chunk_caps.as<int4>();
+    a.heavy = p.heavy.as<int4>();
+    a.heavy_bracket = p.bracket.as<longlong2>();
+    a.heavy_cand = p.heavy_cand.as<int4>();
+    a.n_chunks = p.n_chunks;
+    a.n_heavy = p.n_heavy;
+    a.vis = h->vis.as<uint32_t>();
+    a.vis_cnt = h->vis_cnt.as<uint32_t>();
+    a.cand = h->cand.as<unsigned long long>();
+    a.cand_cnt = h->cand_cnt.as<uint32_t>();
+    a.extra = h->extra.as<uint32_t>();
+    a.extra_cnt = h->extra_cnt.as<uint32_t>();
+    a.flags = h->flags.as<uint32_t>();
+    a.partial = h->partial.as<float>();
+    a.stat_fallback = h->stat.as<unsigned long long>();
+    a.mask_out = nullptr;
+    return a;
+}
+
+// Algorithm 1 on one mode at AO iteration ao_iter.
+ntc_status run_snmc(ntc_handle* h, int mode, double c, uint64_t seed, uint64_t ao_iter) {
+    ntc_status st = build_plan(h, mode, c);
+    if (st != NTC_OK) return st;
+    const ModePlan& p = h->plan[mode];
+    for (int l = 0; l < h->max_inner; ++l) {
+        ModeArgs a = mode_args(h, mode, l, seed, ao_iter);
+        NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, p, h->stream, false,
+                                &h->stats.kernel_launches));
+        h->stats.visits += p.visits;
+        h->stats.visits_heavy += p.visits_heavy;
+        h->stats.rows_updated += p.rows_updated;
+        h->stats.rows_skipped += p.rows_skipped;
+        const int64_t N = h->order, R = h->rank, s = h->storage_bf16 ? 2 : 4;
+        h->stats.alg_bytes += p.visits * ((N - 1) * 4 + 4 + (N - 1) * R * s) +
+                              p.rows_updated * (8 + 4 * R + 4 * R + (h->storage_bf16 ? 2 * R : 0) +
+                                                (h->max_inner > 1 ? 8 * R : 0));
+    }
+    return NTC_OK;
+}
+
+ntc_status check_ready(ntc_handle* h) {
+    if (!h) return NTC_ERR_ARG;
+    if (h->nnz < 0) return fail(h, NTC_ERR_STATE, "ntc_set_observed has not been called");
+    return NTC_OK;
+}
+
+ntc_status reset_stats(ntc_handle* h) {
+    h->stats = ntc_stats{};
+    NTC_CUDA(h, h->stat.ensure(sizeof(unsigned long long)));
+    NTC_CUDA(h, cudaMemsetAsync(h->stat.p, 0, sizeof(unsigned long long), h->stream));
+    return NTC_OK;
+}
+
+// Stable LSD radix sort of (key = row index of `mode`, payload = entry index).
+ntc_status sort_mode(ntc_handle* h, int mode, DevMem& k0, DevMem& k1, DevMem& v0, DevMem& v1, DevMem& hist,
+                     DevMem& sums, uint32_t** keys_out, uint32_t** perm_out) {
+    const int64_t n = h->nnz;
+    cudaStream_t s = h->stream;
+    k_extract_keys<<<grid_for(n), 256, 0, s>>>(h->coo_idx.as<int32_t>(), n, h->order, mode, k0.as<uint32_t>(),
+                                               v0.as<uint32_t>());
+    int bits = 1;
+    while (bits < 31 && (1ll << bits) < h->dims[mode]) ++bits;
+    const int passes = (bits + 7) / 8;
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    const int64_t nh = (int64_t)ntiles * 256;
+    const int nb = (int)((nh + kScanBlock - 1) / kScanBlock);
+    uint32_t *kin = k0.as<uint32_t>(), *vin = v0.as<uint32_t>(), *kout = k1.as<uint32_t>(), *vout = v1.as<uint32_t>();
+    for (int pass = 0; pass < passes && n > 0; ++pass) {
+        const int shift = 8 * pass;
+        k_radix_hist<<<ntiles, kThreads, 0, s>>>(kin, n, shift, hist.as<uint32_t>(), ntiles);
+        k_scan_sums<<<nb, kThreads, 0, s>>>(hist.as<uint32_t>(), nh, sums.as<uint32_t>());
+        k_scan_top<<<1, kThreads, 0, s>>>(sums.as<uint32_t>(), nb);
+        k_scan_apply<<<nb, kThreads, 0, s>>>(hist.as<uint32_t>(), nh, sums.as<uint32_t>(),
+                                             hist.as<uint32_t>() + nh);
+        k_radix_scatter<<<ntiles, kThreads, 0, s>>>(kin, vin, kout, vout, n, shift, hist.as<uint32_t>() + nh, ntiles);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    NTC_CUDA(h, cudaGetLastError());
+    *keys_out = kin;
+    *perm_out = vin;
+    return NTC_OK;
+}
+
+ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, const float* vals, bool dev) {
+    if (!h) return NTC_ERR_ARG;
+    if (nnz < 0 || nnz >= (1ll << 31) || (nnz > 0 && (!idx || !vals)))
+        return fail(h, NTC_ERR_ARG, "nnz must be in [0, 2^31) with non-null idx and vals");
+    cudaStream_t s = h->stream;
+    const int N = h->order;
+    // stage and validate before touching the handle's current data
+    DevMem cidx, cval;
+    NTC_CUDA(h, cidx.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz * N, 1)));
+    NTC_CUDA(h, cval.ensure(sizeof(float) * (size_t)std::max<int64_t>(nnz, 1)));
+    if (nnz > 0) {
+        const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        NTC_CUDA(h, cudaMemcpyAsync(cidx.p, idx, sizeof(int32_t) * nnz * N, kind, s));
+        NTC_CUDA(h, cudaMemcpyAsync(cval.p, vals, sizeof(float) * nnz, kind, s));
+    }
+    DevMem bad;
+    NTC_CUDA(h, bad.ensure(sizeof(unsigned)));
+    NTC_CUDA(h, cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
+    if (nnz > 0) k_validate<<<grid_for(nnz), 256, 0, s>>>(cidx.as<int32_t>(), nnz, N, h->dims_dev.as<int64_t>(),
+                                                         bad.as<unsigned>());
+    unsigned bad_h = 0;
+    NTC_CUDA(h, cudaMemcpyAsync(&bad_h, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    NTC_CUDA(h, cudaStreamSynchronize(s));
+    if (bad_h) return fail(h, NTC_ERR_INDEX, "an observed index is out of range");
+    // commit
+    std::swap(h->coo_idx.p, cidx.p);
+    std::swap(h->coo_idx.bytes, cidx.bytes);
+    std::swap(h->coo_val.p, cval.p);
+    std::swap(h->coo_val.bytes, cval.bytes);
+    h->nnz = nnz;
+    h->ao_iter = 0;
+    for (int i = 0; i < N; ++i) h->plan[i].valid = false;
+    // per-mode buckets
+    DevMem k0, k1, v0, v1, hist, sums;
+    const size_t nb4 = sizeof(uint32_t) * (size_t)std::max<int64_t>(nnz, 1);
+    NTC_CUDA(h, k0.ensure(nb4));
+    NTC_CUDA(h, k1.ensure(nb4));
+    NTC_CUDA(h, v0.ensure(nb4));
+    NTC_CUDA(h, v1.ensure(nb4));
+    const int64_t ntiles = (nnz + kSortTile - 1) / kSortTile;
+    NTC_CUDA(h, hist.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(2 * ntiles * 256, 1)));
+    NTC_CUDA(h, sums.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles * 256 / kScanBlock + 2, 1)));
+    const int EW = ew_of(N);
+    for (int i = 0; i < N; ++i) {
+        uint32_t *keys = nullptr, *perm = nullptr;
+        ntc_status st = sort_mode(h, i, k0, k1, v0, v1, hist, sums, &keys, &perm);
+        if (st != NTC_OK) return st;
+        NTC_CUDA(h, h->row_ptr[i].ensure(sizeof(int64_t) * (size_t)(h->dims[i] + 1)));
+        k_row_ptr<<<grid_for(nnz + 1), 256, 0, s>>>(keys, nnz, h->dims[i], h->row_ptr[i].as<int64_t>());
+        NTC_CUDA(h, h->bucket[i].ensure((size_t)EW * 4 * (size_t)std::max<int64_t>(nnz, 1)));
+        if (nnz > 0) {
+            if (EW == 4)
+                k_fill_bucket<4><<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), perm,
+                                                               nnz, N, i, h->bucket[i].as<Entry<4>>());
+            else
+                k_fill_bucket<8><<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), perm,
+                                                               nnz, N, i, h->bucket[i].as<Entry<8>>());
+        }
+        if (h->keep_perm) {
+            NTC_CUDA(h, h->perm[i].ensure(nb4));
+            NTC_CUDA(h, cudaMemcpyAsync(h->perm[i].p, perm, nb4, cudaMemcpyDeviceToDevice, s));
+        } else {
+            h->perm[i].release();
+        }
+        h->row_ptr_h[i].resize((size_t)h->dims[i] + 1);
+        NTC_CUDA(h, cudaMemcpyAsync(h->row_ptr_h[i].data(), h->row_ptr[i].p, sizeof(int64_t) * (h->dims[i] + 1),
+                                    cudaMemcpyDeviceToHost, s));
+        NTC_CUDA(h, cudaGetLastError());
+    }
+    // initial factors for modes not set by the caller
+    DevMem part, tot;
+    NTC_CUDA(h, part.ensure(sizeof(double) * 1024));
+    NTC_CUDA(h, tot.ensure(sizeof(double)));
+    const int gb = grid_for(nnz, 256, 1024);
+    k_sum_f32<<<gb, kThreads, 0, s>>>(h->coo_val.as<float>(), nnz, part.as<double>());
+    k_sum_partials<<<1, kThreads, 0, s>>>(part.as<double>(), gb, tot.as<double>());
+    for (int i = 0; i < N; ++i) {
+        if (h->factor_set[i]) continue;
+        k_init_factor<<<grid_for(h->dims[i] * h->rp), 256, 0, s>>>(
+            h->U[i].as<float>(), h->storage_bf16 ? h->Ub[i].as<uint16_t>() : nullptr, h->dims[i], h->rank, h->rp, i,
+            tot.as<double>(), nnz, N, (uint32_t)h->init_seed, (uint32_t)(h->init_seed >> 32));
+    }
+    NTC_CUDA(h, cudaGetLastError());
+    NTC_CUDA(h, cudaStreamSynchronize(s));   // temporaries are freed on return
+    return NTC_OK;
+}
+
+FactorSet factor_set(ntc_handle* h) {
+    FactorSet f;
+    for (int i = 0; i < h->order; ++i) f.U[i] = h->U[i].as<float>();
+    f.order = h->order;
+    f.R = h->rank;
+    f.rp = h->rp;
+    return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, ntc_handle** out) {
+    if (!out) return NTC_ERR_ARG;
+    *out = nullptr;
+    if (order < 2 || order > kMaxOrder || !dims || rank < 1 || rank > 64 || !(lambda >= 0.0) || std::isinf(lambda))
+        return NTC_ERR_ARG;
+    for (int i = 0; i < order; ++i)
+        if (dims[i] < 1 || dims[i] >= (1ll << 31)) return NTC_ERR_ARG;
+    ntc_handle* h = new (std::nothrow) ntc_handle();
+    if (!h) return NTC_ERR_OOM;
+    h->order = order;
+    h->rank = rank;
+    h->rp = pad_rank(rank);
+    h->lambda = lambda;
+    cudaGetDevice(&h->device);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < order && e == cudaSuccess; ++i) {
+        h->dims[i] = dims[i];
+        const size_t bytes = sizeof(float) * (size_t)dims[i] * h->rp;
+        e = h->U[i].ensure(bytes);
+        if (e == cudaSuccess) e = cudaMemset(h->U[i].p, 0, bytes);
+    }
+    if (e == cudaSuccess) e = h->dims_dev.ensure(sizeof(int64_t) * kMaxOrder);
+    if (e == cudaSuccess) e = cudaMemcpy(h->dims_dev.p, h->dims, sizeof(int64_t) * kMaxOrder, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        const ntc_status s = e == cudaErrorMemoryAllocation ? NTC_ERR_OOM : NTC_ERR_CUDA;
+        delete h;
+        return s;
+    }
+    *out = h;
+    return NTC_OK;
+}
+
+ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
+    if (!h || !key) return NTC_ERR_ARG;
+    h->err.clear();
+    const std::string k(key);
+    if (k == "max_inner") {
+        if (!(v >= 1 && v <= 1e6)) return fail(h, NTC_ERR_ARG, "max_inner must be >= 1");
+        h->max_inner = (int)v;
+        if (h->max_inner > 1) {
+            int64_t mx = 0;
+            for (int i = 0; i < h->order; ++i) mx = std::max(mx, h->dims[i]);
+            NTC_CUDA(h, h->Y.ensure(sizeof(float) * (size_t)mx * h->rp));
+        }
+    } else if (k == "power_iters") {
+        if (!(v >= 1 && v <= 1e4)) return fail(h, NTC_ERR_ARG, "power_iters must be in [1, 10000]");
+        h->power_iters = (int)v;
+    } else if (k == "storage_bf16") {
+        const int b = v != 0.0;
+        if (b && !h->storage_bf16) {
+            for (int i = 0; i < h->order; ++i) {
+                const int64_t n = h->dims[i] * h->rp;
+                NTC_CUDA(h, h->Ub[i].ensure(sizeof(uint16_t) * (size_t)n));
+                k_to_bf16<<<grid_for(n), 256, 0, h->stream>>>(h->U[i].as<float>(), h->Ub[i].as<uint16_t>(), n);
+            }
+            NTC_CUDA(h, cudaGetLastError());
+        }
+        h->storage_bf16 = b;
+    } else if (k == "init_seed") {
+        if (!(v >= 0)) return fail(h, NTC_ERR_ARG, "init_seed must be >= 0");
+        h->init_seed = (uint64_t)v;
+    } else if (k == "keep_perm") {
+        h->keep_perm = v != 0.0;
+    } else if (k == "bracket_z") {
+        if (!(v >= 0 && v <= 1e6)) return fail(h, NTC_ERR_ARG, "bracket_z must be in [0, 1e6]");
+        h->bracket_z = v;
+    } else if (k == "heavy_rows") {
+        if (!(v >= 64 && v <= kLightMax)) return fail(h, NTC_ERR_ARG, "heavy_rows must be in [64, 4096]");
+        h->heavy_threshold = (int)v;
+    } else if (k == "chunk") {
+        if (!(v >= 256 && v <= (1 << 24))) return fail(h, NTC_ERR_ARG, "chunk must be in [256, 2^24]");
+        h->chunk = (int)v;
+    } else {
+        return fail(h, NTC_ERR_ARG, "unknown parameter " + k);
+    }
+    return NTC_OK;
+}
+
+ntc_status ntc_set_stream(ntc_handle* h, void* stream) {
+    if (!h) return NTC_ERR_ARG;
+    h->err.clear();
+    h->stream = static_cast<cudaStream_t>(stream);
+    return NTC_OK;
+}
+
+ntc_status ntc_set_observed(ntc_handle* h, int64_t nnz, const int32_t* idx, const float* vals) {
+    if (h) h->err.clear();
+    return set_observed_impl(h, nnz, idx, vals, false);
+}
+
+ntc_status ntc_set_observed_dev(ntc_handle* h, int64_t nnz, const int32_t* idx, const float* vals) {
+    if (h) h->err.clear();
+    return set_observed_impl(h, nnz, idx, vals, true);
+}
+
+ntc_status ntc_epoch(ntc_handle* h, const int* mode_order, double c, uint64_t seed) {
+    ntc_status st = check_ready(h);
+    if (st != NTC_OK) return st;
+    h->err.clear();
+    if (!(c > 0.0 && c <= 1.0)) return fail(h, NTC_ERR_ARG, "c must be in (0, 1]");
+    int ord[kMaxOrder];
+    bool seen[kMaxOrder] = {};
+    for (int i = 0; i < h->order; ++i) {
+        ord[i] = mode_order ? mode_order[i] : i;
+        if (ord[i] < 0 || ord[i] >= h->order || seen[ord[i]])
+            return fail(h, NTC_ERR_ARG, "mode_order must be a permutation of 0..order-1");
+        seen[ord[i]] = true;
+    }
+    for (int i = 0; i < h->order; ++i)
+        if ((st = build_plan(h, i, c)) != NTC_OK) return st;
+    if ((st = reset_stats(h)) != NTC_OK) return st;
+    const int64_t T = (int64_t)std::ceil(1.0 / c - 1e-12);   // AO iterations per epoch
+    for (int64_t t = 0; t < T; ++t) {
+        for (int i = 0; i < h->order; ++i)
+            if ((st = run_snmc(h, ord[i], c, seed, h->ao_iter)) != NTC_OK) return st;
+        h->ao_iter += 1;
+    }
+    return NTC_OK;
+}
+
+ntc_status ntc_snmc(ntc_handle* h, int mode, double c, uint64_t seed) {
+    ntc_status st = check_ready(h);
+    if (st != NTC_OK) return st;
+    h->err.clear();
+    if (mode < 0 || mode >= h->order) return fail(h, NTC_ERR_ARG, "mode out of range");
+    if (!(c > 0.0 && c <= 1.0)) return fail(h, NTC_ERR_ARG, "c must be in (0, 1]");
+    if ((st = reset_stats(h)) != NTC_OK) return st;
+    return run_snmc(h, mode, c, seed, h->ao_iter);
+}
+
+ntc_status ntc_predict_dev(ntc_handle* h, int64_t n, const int32_t* idx, float* out) {
+    if (!h || n < 0 || (n > 0 && (!idx || !out))) return NTC_ERR_ARG;
+    h->err.clear();
+    if (n == 0) return NTC_OK;
+    k_predict<<<grid_for(n), 256, 0, h->stream>>>(factor_set(h), idx, n, out);
+    NTC_CUDA(h, cudaGetLastError());
+    return NTC_OK;
+}
+
+static bool indices_ok(const ntc_handle* h, int64_t n, const int32_t* idx) {
+    for (int64_t e = 0; e < n; ++e)
+        for (int i = 0; i < h->order; ++i) {
+            const int32_t v = idx[e * h->order + i];
+            if (v < 0 || v >= h->dims[i]) return false;
+        }
+    return true;
+}
+
+ntc_status ntc_predict(ntc_handle* h, int64_t n, const int32_t* idx, float* out) {
+    if (!h || n < 0 || (n > 0 && (!idx || !out))) return NTC_ERR_ARG;
+    h->err.clear();
+    if (n == 0) return NTC_OK;
+    if (!indices_ok(h, n, idx)) return fail(h, NTC_ERR_INDEX, "a query index is out of range");
+    DevMem di, dout;
+    NTC_CUDA(h, di.ensure(sizeof(int32_t) * n * h->order));
+    NTC_CUDA(h, dout.ensure(sizeof(float) * n));
+    NTC_CUDA(h, cudaMemcpyAsync(di.p, idx, sizeof(int32_t) * n * h->order, cudaMemcpyHostToDevice, h->stream));
+    k_predict<<<grid_for(n), 256, 0, h->stream>>>(factor_set(h), di.as<int32_t>(), n, dout.as<float>());
+    NTC_CUDA(h, cudaGetLastError());
+    NTC_CUDA(h, cudaMemcpyAsync(out, dout.p, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return NTC_OK;
+}
+
+ntc_status ntc_rmse(ntc_handle* h, int64_t n, const int32_t* idx, const float* vals, double* out) {
+    if (!h || !out || n < 0 || (n > 0 && (!idx || !vals))) return NTC_ERR_ARG;
+    h->err.clear();
+    if (n == 0) {
+        *out = 0.0;
+        return NTC_OK;
+    }
+    if (!indices_ok(h, n, idx)) return fail(h, NTC_ERR_INDEX, "a query index is out of range");
+    DevMem di, dv, part, tot;
+    NTC_CUDA(h, di.ensure(sizeof(int32_t) * n * h->order));
+    NTC_CUDA(h, dv.ensure(sizeof(float) * n));
+    NTC_CUDA(h, part.ensure(sizeof(double) * 1024));
+    NTC_CUDA(h, tot.ensure(sizeof(double)));
+    NTC_CUDA(h, cudaMemcpyAsync(di.p, idx, sizeof(int32_t) * n * h->order, cudaMemcpyHostToDevice, h->stream));
+    NTC_CUDA(h, cudaMemcpyAsync(dv.p, vals, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+    const int gb = grid_for(n, 256, 1024);
+    k_sq_resid<<<gb, kThreads, 0, h->stream>>>(factor_set(h), di.as<int32_t>(), dv.as<float>(), n, part.as<double>());
+    k_sum_partials<<<1, kThreads, 0, h->stream>>>(part.as<double>(), gb, tot.as<double>());
+    NTC_CUDA(h, cudaGetLastError());
+    double s = 0.0;
+    NTC_CUDA(h, cudaMemcpyAsync(&s, tot.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    *out = std::sqrt(s / (double)n);
+    return NTC_OK;
+}
+
+ntc_status ntc_cost(ntc_handle* h, double* out) {
+    ntc_status st = check_ready(h);
+    if (st != NTC_OK) return st;
+    if (!out) return fail(h, NTC_ERR_ARG, "out is null");
+    h->err.clear();
+    DevMem part, tot;
+    NTC_CUDA(h, part.ensure(sizeof(double) * 1024));
+    NTC_CUDA(h, tot.ensure(sizeof(double) * (kMaxOrder + 1)));
+    double fit = 0.0, reg = 0.0;
+    const int gb = grid_for(h->nnz, 256, 1024);
+    k_sq_resid<<<gb, kThreads, 0, h->stream>>>(factor_set(h), h->coo_idx.as<int32_t>(), h->coo_val.as<float>(),
+                                               h->nnz, part.as<double>());
+    k_sum_partials<<<1, kThreads, 0, h->stream>>>(part.as<double>(), gb, tot.as<double>());
+    for (int i = 0; i < h->order; ++i) {
+        const int64_t n = h->dims[i] * h->rp;   // padding columns are zero
+        const int g2 = grid_for(n, 256, 1024);
+        k_sq_sum<<<g2, kThreads, 0, h->stream>>>(h->U[i].as<float>(), n, part.as<double>());
+        k_sum_partials<<<1, kThreads, 0, h->stream>>>(part.as<double>(), g2, tot.as<double>() + 1 + i);
+    }
+    NTC_CUDA(h, cudaGetLastError());
+    double t[kMaxOrder + 1];
+    NTC_CUDA(h, cudaMemcpyAsync(t, tot.p, sizeof(double) * (h->order + 1), cudaMemcpyDeviceToHost, h->stream));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    fit = t[0];
+    for (int i = 0; i < h->order; ++i) reg += t[1 + i];
+    *out = 0.5 * fit + 0.5 * h->lambda * reg;
+    return NTC_OK;
+}
+
+ntc_status ntc_get_factor(ntc_handle* h, int mode, float* out) {
+    if (!h || !out || mode < 0 || mode >= h->order) return NTC_ERR_ARG;
+    h->err.clear();
+    NTC_CUDA(h, cudaMemcpy2DAsync(out, sizeof(float) * h->rank, h->U[mode].p, sizeof(float) * h->rp,
+                                  sizeof(float) * h->rank, (size_t)h->dims[mode], cudaMemcpyDeviceToHost, h->stream));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return NTC_OK;
+}
+
+ntc_status ntc_set_factor(ntc_handle* h, int mode, const float* in) {
+    if (!h || !in || mode < 0 || mode >= h->order) return NTC_ERR_ARG;
+    h->err.clear();
+    const int64_t n = h->dims[mode] * (int64_t)h->rank;
+    for (int64_t j = 0; j < n; ++j)
+        if (!(in[j] >= 0.0f) || std::isinf(in[j])) return fail(h, NTC_ERR_ARG, "factor entries must be finite and >= 0");
+    NTC_CUDA(h, cudaMemsetAsync(h->U[mode].p, 0, sizeof(float) * h->dims[mode] * h->rp, h->stream));
+    NTC_CUDA(h, cudaMemcpy2DAsync(h->U[mode].p, sizeof(float) * h->rp, in, sizeof(float) * h->rank,
+                                  sizeof(float) * h->rank, (size_t)h->dims[mode], cudaMemcpyHostToDevice, h->stream));
+    if (h->storage_bf16) {
+        const int64_t m = h->dims[mode] * h->rp;
+        k_to_bf16<<<grid_for(m), 256, 0, h->stream>>>(h->U[mode].as<float>(), h->Ub[mode].as<uint16_t>(), m);
+        NTC_CUDA(h, cudaGetLastError());
+    }
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->factor_set[mode] = true;
+    return NTC_OK;
+}
+
+ntc_status ntc_get_state(ntc_handle* h, uint64_t* ao_iter) {
+    if (!h || !ao_iter) return NTC_ERR_ARG;
+    *ao_iter = h->ao_iter;
+    return NTC_OK;
+}
+
+ntc_status ntc_set_state(ntc_handle* h, uint64_t ao_iter) {
+    if (!h) return NTC_ERR_ARG;
+    h->ao_iter = ao_iter;
+    return NTC_OK;
+}
+
+ntc_status ntc_sync(ntc_handle* h) {
+    if (!h) return NTC_ERR_ARG;
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return NTC_OK;
+}
+
+ntc_status ntc_get_stats(ntc_handle* h, ntc_stats* out) {
+    if (!h || !out) return NTC_ERR_ARG;
+    *out = h->stats;
+    if (h->stat.p) {
+        unsigned long long fb = 0;
+        NTC_CUDA(h, cudaMemcpyAsync(&fb, h->stat.p, sizeof(fb), cudaMemcpyDeviceToHost, h->stream));
+        NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+        out->fallback_rows = (int64_t)fb;
+    }
+    return NTC_OK;
+}
+
+ntc_status ntc_get_bucket(ntc_handle* h, int mode, int64_t* row_ptr, int64_t* perm) {
+    ntc_status st = check_ready(h);
+    if (st != NTC_OK) return st;
+    if (mode < 0 || mode >= h->order) return fail(h, NTC_ERR_ARG, "mode out of range");
+    if (row_ptr)
+        memcpy(row_ptr, h->row_ptr_h[mode].data(), sizeof(int64_t) * (size_t)(h->dims[mode] + 1));
+    if (perm) {
+        if (!h->perm[mode].p) return fail(h, NTC_ERR_STATE, "set keep_perm before ntc_set_observed");
+        std::vector<uint32_t> p((size_t)h->nnz);
+        NTC_CUDA(h, cudaMemcpyAsync(p.data(), h->perm[mode].p, sizeof(uint32_t) * h->nnz, cudaMemcpyDeviceToHost,
+                                    h->stream));
+        NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (int64_t q = 0; q < h->nnz; ++q) perm[q] = p[(size_t)q];
+    }
+    return NTC_OK;
+}
+
+ntc_status ntc_sample_mask(ntc_handle* h, int mode, double c, uint64_t seed, uint64_t ao_iter, int inner,
+                           uint8_t* mask) {
+    ntc_status st = check_ready(h);
+    if (st != NTC_OK) return st;
+    h->err.clear();
+    if (mode < 0 || mode >= h->order || !mask || inner < 0) return fail(h, NTC_ERR_ARG, "bad sampler arguments");
+    if (!(c > 0.0 && c <= 1.0)) return fail(h, NTC_ERR_ARG, "c must be in (0, 1]");
+    if ((st = build_plan(h, mode, c)) != NTC_OK) return st;
+    if ((st = reset_stats(h)) != NTC_OK) return st;
+    NTC_CUDA(h, h->mask.ensure((size_t)std::max<int64_t>(h->nnz, 1)));
+    NTC_CUDA(h, cudaMemsetAsync(h->mask.p, 0, (size_t)std::max<int64_t>(h->nnz, 1), h->stream));
+    ModeArgs a = mode_args(h, mode, inner, seed, ao_iter);
+    a.mask_out = h->mask.as<uint8_t>();
+    NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, h->plan[mode], h->stream, true,
+                            &h->stats.kernel_launches));
+    NTC_CUDA(h, cudaMemcpyAsync(mask, h->mask.p, (size_t)h->nnz, cudaMemcpyDeviceToHost, h->stream));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return NTC_OK;
+}
+
+const char* ntc_last_error(const ntc_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+void ntc_destroy(ntc_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+}  // extern "C"

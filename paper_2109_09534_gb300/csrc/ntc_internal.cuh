@@ -1,0 +1,154 @@
+// ntc_internal.cuh -- shared device helpers and kernel argument layouts of the
+// GB300 tensor-completion library.  Nothing here is visible through the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ntc {
+
+constexpr int kMaxOrder = 8;
+constexpr int kThreads = 256;        // threads per block of every row/chunk kernel
+constexpr int kLightMax = 4096;      // largest row whose keys fit in shared memory
+
+// Bucket entry of one observation, seen from the mode being updated: the other
+// modes' indices in increasing mode order, then the value in the last word.
+// EW = 4 words (16 B, one 128-bit load) for order <= 4, else 8 words (32 B).
+template <int EW>
+struct alignas(EW * 4) Entry {
+    int32_t w[EW];
+};
+
+// ---- Philox4x32-10 (Salmon et al., SC'11): two 32x32 multiplies per round,
+// high halves xored with the other words and the round key; Weyl key bumps.
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c0;
+}
+
+__device__ __forceinline__ uint4 philox4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                         uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Sampling stream of one (mode, AO iteration, inner iteration): the key of
+// bucket position q is word 0 of Philox(counter {mode, k, l, q}, key seed).
+struct SampleStream {
+    uint32_t mode, iter, inner, k0, k1;
+    __device__ __forceinline__ uint32_t key(uint32_t q) const {
+        return philox_word0(mode, iter, inner, q, k0, k1);
+    }
+};
+
+// ---- bfloat16 storage helpers (round to nearest even on store).
+__device__ __forceinline__ float4 bf16x4_to_f32(uint2 v) {
+    float4 r;
+    r.x = __uint_as_float(v.x << 16);
+    r.y = __uint_as_float(v.x & 0xFFFF0000u);
+    r.z = __uint_as_float(v.y << 16);
+    r.w = __uint_as_float(v.y & 0xFFFF0000u);
+    return r;
+}
+
+__device__ __forceinline__ uint16_t f32_to_bf16_rne(float f) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+// ---- block-wide exclusive scan of one int per thread (kThreads threads).
+// `tmp` holds kThreads/32 + 1 ints.  Returns the exclusive prefix; *total gets
+// the block sum.  Contains __syncthreads.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* tmp, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < kThreads / 32 ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kThreads / 32) tmp[lane] = w;   // inclusive warp prefix
+        if (lane == kThreads / 32 - 1) tmp[kThreads / 32] = w;
+    }
+    __syncthreads();
+    const int before = warp > 0 ? tmp[warp - 1] : 0;
+    *total = tmp[kThreads / 32];
+    const int r = before + x - v;
+    __syncthreads();
+    return r;
+}
+
+// ---- the arguments of one mode update (Alg. 1 on mode `mode`).
+struct ModeArgs {
+    // other modes' factors as gathered (float32 or bfloat16), in increasing
+    // mode order with `mode` left out; row stride rp elements
+    const void* other[kMaxOrder - 1];
+    int n_other;
+    int rank;        // R
+    int rp;          // padded row length (8, 16, 32, 64)
+    float lambda;
+    double lambda_d;
+    int power_iters;
+    // updated mode
+    float* U;                 // float32 master A_l, [I][rp]
+    uint16_t* Ub;             // bfloat16 copy (or null)
+    float* Y;                 // extrapolation buffer Y_l (null when MAX_INNER = 1)
+    int read_y;               // 1: gradient point Y_l read from Y, 0: from U (l = 0)
+    int write_y;              // 1: store Y_{l+1}
+    const int64_t* row_ptr;   // bucket row pointers of `mode`
+    const void* bucket;       // Entry<EW>[nnz]
+    SampleStream ss;
+    // light rows
+    const int32_t* light_rows;
+    const int32_t* light_k;
+    // heavy rows
+    const int4* chunks;       // {heavy index, pos_begin, pos_end, cand_off}
+    const int4* chunk_caps;   // {cand_cap, 0, 0, 0}
+    const int4* heavy;        // {row, k, chunk_begin, chunk_end}
+    const longlong2* heavy_bracket;  // {lo, hi}: key < lo certain, lo <= key < hi candidate
+    const int4* heavy_cand;   // {cand_begin, cand_total_cap, extra_off, extra_cap}
+    int n_chunks;
+    int n_heavy;
+    uint32_t* vis;            // visit lists of chunks, indexed by bucket position
+    uint32_t* vis_cnt;        // [n_chunks]
+    unsigned long long* cand; // (key << 32 | position) candidates
+    uint32_t* cand_cnt;       // [n_chunks]
+    uint32_t* extra;          // chosen candidates per heavy row
+    uint32_t* extra_cnt;      // [n_heavy]
+    uint32_t* flags;          // [n_heavy]: 1 = candidate overflow
+    float* partial;           // [(n_chunks + n_heavy)][pw]
+    unsigned long long* stat_fallback;  // counter of rows that used the exact selector
+    uint8_t* mask_out;        // sampler-only mode: mask over bucket positions
+};
+
+}  // namespace ntc

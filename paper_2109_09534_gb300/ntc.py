@@ -1,0 +1,234 @@
+"""Thin ctypes binding of the C ABI in ``include/ntc.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libntc.so``.  The functions keep the C names; :class:`NTC` wraps a handle
+for convenience.  Host arrays are numpy arrays; ``*_dev`` calls take device
+pointers (for example ``torch.Tensor.data_ptr()``).  There is no fallback: if
+the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ntc.h")
+
+NTC_OK, NTC_ERR_ARG, NTC_ERR_INDEX, NTC_ERR_OOM, NTC_ERR_STATE, NTC_ERR_CUDA = range(6)
+_STATUS = {0: "NTC_OK", 1: "NTC_ERR_ARG", 2: "NTC_ERR_INDEX", 3: "NTC_ERR_OOM", 4: "NTC_ERR_STATE",
+           5: "NTC_ERR_CUDA"}
+
+
+class NTCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ntc_stats(ctypes.Structure):
+    _fields_ = [("visits", ctypes.c_int64), ("visits_heavy", ctypes.c_int64),
+                ("rows_updated", ctypes.c_int64), ("rows_skipped", ctypes.c_int64),
+                ("fallback_rows", ctypes.c_int64), ("alg_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def declared_functions() -> list:
+    """Names of the functions declared in include/ntc.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ntc_[a-z_]+)\s*\(", src)))
+
+
+def load(path: Optional[str] = None):
+    """Load libntc.so (built in-tree by build.py).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build the CUDA library first "
+                      "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    P, i64, u64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
+    sig = {
+        "ntc_create": [i32, P, i32, dbl, ctypes.POINTER(P)],
+        "ntc_set_param": [P, ctypes.c_char_p, dbl],
+        "ntc_set_stream": [P, P],
+        "ntc_set_observed": [P, i64, P, P],
+        "ntc_set_observed_dev": [P, i64, P, P],
+        "ntc_epoch": [P, P, dbl, u64],
+        "ntc_snmc": [P, i32, dbl, u64],
+        "ntc_predict": [P, i64, P, P],
+        "ntc_predict_dev": [P, i64, P, P],
+        "ntc_rmse": [P, i64, P, P, ctypes.POINTER(dbl)],
+        "ntc_cost": [P, ctypes.POINTER(dbl)],
+        "ntc_get_factor": [P, i32, P],
+        "ntc_set_factor": [P, i32, P],
+        "ntc_get_state": [P, ctypes.POINTER(u64)],
+        "ntc_set_state": [P, u64],
+        "ntc_sync": [P],
+        "ntc_get_stats": [P, ctypes.POINTER(ntc_stats)],
+        "ntc_get_bucket": [P, i32, P, P],
+        "ntc_sample_mask": [P, i32, dbl, u64, u64, i32, P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.ntc_last_error.argtypes = [P]
+    L.ntc_last_error.restype = ctypes.c_char_p
+    L.ntc_destroy.argtypes = [P]
+    L.ntc_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(h, status: int) -> None:
+    if status != NTC_OK:
+        msg = load().ntc_last_error(h) if h else b""
+        raise NTCError(status, (msg or b"").decode())
+
+
+class NTC:
+    """One completion problem on the current CUDA device (a C handle)."""
+
+    def __init__(self, dims: Sequence[int], rank: int, lam: float, stream: Optional[int] = None,
+                 **params):
+        L = load()
+        self.dims = [int(d) for d in dims]
+        self.order = len(self.dims)
+        self.rank = int(rank)
+        d = np.ascontiguousarray(self.dims, dtype=np.int64)
+        h = ctypes.c_void_p()
+        st = L.ntc_create(self.order, _ptr(d), self.rank, float(lam), ctypes.byref(h))
+        if st != NTC_OK:
+            raise NTCError(st, "ntc_create failed")
+        self.h = h
+        self.L = L
+        if stream is not None:
+            _check(self.h, L.ntc_set_stream(self.h, ctypes.c_void_p(stream)))
+        for k, v in params.items():
+            self.set_param(k, v)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.L.ntc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_param(self, key: str, value: float) -> None:
+        _check(self.h, self.L.ntc_set_param(self.h, key.encode(), float(value)))
+
+    def set_stream(self, stream: int) -> None:
+        _check(self.h, self.L.ntc_set_stream(self.h, ctypes.c_void_p(stream)))
+
+    def set_observed(self, idx: np.ndarray, vals: np.ndarray) -> None:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float32)
+        if idx.shape != (vals.shape[0], self.order):
+            raise ValueError("idx must be [nnz][order] and vals [nnz]")
+        _check(self.h, self.L.ntc_set_observed(self.h, vals.shape[0], _ptr(idx), _ptr(vals)))
+
+    def set_observed_ptr(self, nnz: int, idx_ptr: int, vals_ptr: int, device: bool) -> None:
+        f = self.L.ntc_set_observed_dev if device else self.L.ntc_set_observed
+        _check(self.h, f(self.h, int(nnz), ctypes.c_void_p(idx_ptr), ctypes.c_void_p(vals_ptr)))
+
+    def epoch(self, c: float, seed: int, mode_order: Optional[Sequence[int]] = None) -> None:
+        mo = None
+        if mode_order is not None:
+            self._mo = np.ascontiguousarray(mode_order, dtype=np.int32)
+            mo = _ptr(self._mo)
+        _check(self.h, self.L.ntc_epoch(self.h, mo, float(c), int(seed)))
+
+    def snmc(self, mode: int, c: float, seed: int) -> None:
+        _check(self.h, self.L.ntc_snmc(self.h, int(mode), float(c), int(seed)))
+
+    def predict(self, idx: np.ndarray) -> np.ndarray:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        out = np.zeros(idx.shape[0], dtype=np.float32)
+        _check(self.h, self.L.ntc_predict(self.h, idx.shape[0], _ptr(idx), _ptr(out)))
+        return out
+
+    def predict_dev(self, n: int, idx_ptr: int, out_ptr: int) -> None:
+        _check(self.h, self.L.ntc_predict_dev(self.h, int(n), ctypes.c_void_p(idx_ptr),
+                                              ctypes.c_void_p(out_ptr)))
+
+    def rmse(self, idx: np.ndarray, vals: np.ndarray) -> float:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float32)
+        out = ctypes.c_double()
+        _check(self.h, self.L.ntc_rmse(self.h, idx.shape[0], _ptr(idx), _ptr(vals), ctypes.byref(out)))
+        return out.value
+
+    def cost(self) -> float:
+        out = ctypes.c_double()
+        _check(self.h, self.L.ntc_cost(self.h, ctypes.byref(out)))
+        return out.value
+
+    def get_factor(self, mode: int) -> np.ndarray:
+        out = np.zeros((self.dims[mode], self.rank), dtype=np.float32)
+        _check(self.h, self.L.ntc_get_factor(self.h, int(mode), _ptr(out)))
+        return out
+
+    def set_factor(self, mode: int, U: np.ndarray) -> None:
+        U = np.ascontiguousarray(U, dtype=np.float32)
+        if U.shape != (self.dims[mode], self.rank):
+            raise ValueError("factor shape")
+        _check(self.h, self.L.ntc_set_factor(self.h, int(mode), _ptr(U)))
+
+    def factors(self):
+        return [self.get_factor(i) for i in range(self.order)]
+
+    @property
+    def ao_iter(self) -> int:
+        v = ctypes.c_uint64()
+        _check(self.h, self.L.ntc_get_state(self.h, ctypes.byref(v)))
+        return int(v.value)
+
+    @ao_iter.setter
+    def ao_iter(self, k: int) -> None:
+        _check(self.h, self.L.ntc_set_state(self.h, int(k)))
+
+    def sync(self) -> None:
+        _check(self.h, self.L.ntc_sync(self.h))
+
+    def stats(self) -> dict:
+        s = ntc_stats()
+        _check(self.h, self.L.ntc_get_stats(self.h, ctypes.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in ntc_stats._fields_}
+
+    def get_bucket(self, mode: int, perm: bool = False):
+        rp = np.zeros(self.dims[mode] + 1, dtype=np.int64)
+        pm = None
+        if perm:
+            nnz = None
+            pm = np.zeros(max(self._nnz_hint(rp, mode), 1), dtype=np.int64)
+        _check(self.h, self.L.ntc_get_bucket(self.h, int(mode), _ptr(rp), _ptr(pm) if pm is not None else None))
+        if pm is not None:
+            pm = pm[:rp[-1]]
+        return rp, pm
+
+    def _nnz_hint(self, rp, mode):
+        _check(self.h, self.L.ntc_get_bucket(self.h, int(mode), _ptr(rp), None))
+        return int(rp[-1])
+
+    def sample_mask(self, mode: int, c: float, seed: int, ao_iter: int, inner: int, nnz: int) -> np.ndarray:
+        m = np.zeros(max(nnz, 1), dtype=np.uint8)
+        _check(self.h, self.L.ntc_sample_mask(self.h, int(mode), float(c), int(seed), int(ao_iter),
+                                              int(inner), _ptr(m)))
+        return m[:nnz]
