@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput of AO accelerated stochastic nonnegative tensor completion on one
+GB300: observed entries per second per AO epoch, and the fraction of the HBM
+roofline that the algorithmic-bytes model of the sampled visits reaches.
+
+Workload: a 10^4 x 10^4 x 10^4 tensor, rank 32, 100M observation draws whose
+indices follow Zipf(1.1) over a seeded row permutation in every mode, planted
+U[0, 1] factors, sigma = 0.01 Gaussian noise, 2% held out (98M train entries),
+minibatch fraction c = 0.1, MAX_INNER = 1, float32 factors.  One step is one
+epoch: ceil(1/c) = 10 AO iterations over the 3 modes (Sec. IV epoch).
+
+--impl reference times the FP64 CPU oracle (OpenMP over rows, the paper's
+Algorithm 3 design) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "observed entries/s per AO epoch"
+UNIT = "entries/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ntc", choices=["ntc", "reference"])
+    ap.add_argument("--nnz", type=int, default=100_000_000, help="observation draws (2%% held out)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage-bf16", action="store_true")
+    return ap.parse_args()
+
+
+def workload(nnz):
+    from paper_2109_09534_gb300 import synth
+    return synth.zipf_1e4cube(nnz_total=nnz)
+
+
+def config(p, args):
+    return {
+        "workload": f"zipf1.1 10000^3 tensor, R=32, {args.nnz // 1_000_000}M draws "
+                    f"({p.nnz} train), c=0.1, MAX_INNER=1, "
+                    f"{'bf16' if args.storage_bf16 else 'fp32'} factor storage",
+        "dims": p.dims, "rank": p.rank, "nnz_train": p.nnz, "c": p.c, "lambda": p.lam,
+        "step": "one epoch = 10 AO iterations x 3 modes",
+        "l2": "inputs larger than L2: 3 per-mode buckets of 16 B/entry (~4.7 GB) re-read every epoch",
+        "parallelism": "replicas" if args.gpus > 1 else "single GPU",
+    }
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2109_09534_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel sources are unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None
+    if d.get("csrc_sha256_16") != csrc_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    return k.get("dram_bytes_per_launch_full_size")
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.device_id = device_id
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ntc_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device_id), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("gloo")
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([x], dtype=torch.float64)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as td
+        td.barrier()
+
+
+def cpu_baseline(p, steps=1, warmup=0):
+    """The FP64 oracle as it stands, OpenMP over rows (the paper's Algorithm 3),
+    on the host cores.  Bounded sample: one call of Algorithm 1 on mode 0 of the
+    full workload; an epoch is 3 modes x 10 AO iterations of such calls (the
+    three modes are statistically identical here), so the epoch time is
+    estimated as 30x the sampled call."""
+    import numpy as np
+
+    import oracle
+    o = oracle.Oracle(p.dims, p.rank, p.lam, omp=True)
+    o.set_observed(p.idx_train, p.val_train.astype(np.float64))
+    o.init_factors(3)
+    for w in range(warmup):
+        o.ao_iter = 1000 + w
+        o.snmc(0, p.c, seed=4)
+    times = []
+    for s in range(steps):
+        o.ao_iter = s
+        t0 = time.perf_counter()
+        o.snmc(0, p.c, seed=4)
+        times.append(time.perf_counter() - t0)
+    t_epoch = statistics.median(times) * 3 * int(np.ceil(1.0 / p.c - 1e-12))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": p.nnz / t_epoch, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+            "kind": "oracle",
+            "sample": f"one Algorithm-1 call (mode 0, c={p.c}) on the full {p.nnz}-entry workload, "
+                      f"{statistics.median(times):.2f} s median of {steps}; epoch = 30 such calls"}, times
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return
+    p = workload(args.nnz)
+    cb, times = cpu_baseline(p, steps=args.steps, warmup=args.warmup)
+    v = cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": p.nnz / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(p, args), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ntc(args):
+    import numpy as np
+    import torch
+
+    from paper_2109_09534_gb300 import ntc
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    p = workload(args.nnz)
+    params = dict(profile=1)
+    if args.storage_bf16:
+        params["storage_bf16"] = 1
+    g = ntc.NTC(p.dims, p.rank, p.lam, stream=stream.cuda_stream, **params)
+    g.set_observed(p.idx_train, p.val_train)
+    fp32_peak = ntc.measure_fp32_peak(stream.cuda_stream)
+
+    for w in range(args.warmup):
+        g.epoch(p.c, seed=1000 + w)
+    g.sync()
+    g.profile()   # clear the warm-up launches
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        dev_id = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+    except Exception:
+        dev_id = local
+    clocks = Clocks(dev_id)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    alg_bytes = 0
+    visits = 0
+    for s in range(args.steps):
+        g.epoch(p.c, seed=4 + s)
+        st = g.stats()
+        launches += st["kernel_launches"]
+        alg_bytes += st["alg_bytes"]
+        visits += st["visits"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(ws)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws)
+    prof = g.profile()
+
+    ms_step = ms / args.steps
+    value = ws * p.nnz * args.steps / (ms * 1e-3)
+    hbm, hbm_kind = peaks()
+    # dominant kernel and its roofline
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    per_launch_ms = d["ms"] / max(d["launches"], 1)
+    bytes_per_launch = d["alg_bytes"] / max(d["launches"], 1)
+    achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
+    kname = {"light": "k_light", "heavy_sample": "k_heavy_sample", "heavy_resolve": "k_heavy_resolve",
+             "heavy_gram": "k_heavy_gram", "heavy_finish": "k_heavy_finish"}[dom]
+    total_k = sum(v["ms"] for v in prof.values())
+    R, N = p.rank, p.order
+    flops_per_visit = (N - 2) * R + 2 * R + R * (R + 1)
+    gram_flops = prof["heavy_gram"]["alg_bytes"] // ((N - 1) * 4 + 4 + (N - 1) * R * 4) * flops_per_visit
+    gram_tf = gram_flops / (prof["heavy_gram"]["ms"] * 1e-3) / 1e12 if prof["heavy_gram"]["ms"] > 0 else 0.0
+
+    # end to end through the C ABI with pinned host buffers
+    idx_pin = torch.from_numpy(np.ascontiguousarray(p.idx_train)).pin_memory()
+    val_pin = torch.from_numpy(np.ascontiguousarray(p.val_train)).pin_memory()
+    h2d = idx_pin.numel() * 4 + val_pin.numel() * 4
+    d2h = sum(d_ * R * 4 for d_ in p.dims)
+    e2e_times = []
+    g.set_param("profile", 0)
+    for s in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_observed_ptr(p.nnz, idx_pin.data_ptr(), val_pin.data_ptr(), device=False)
+        g.epoch(p.c, seed=77 + s)
+        _ = g.factors()
+        torch.cuda.synchronize()
+        if s > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_t = max_over_ranks(statistics.median(e2e_times), ws) if e2e_times else None
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16-storage/f32" if args.storage_bf16 else "f32",
+            "data": "synthetic", "config": config(p, args), "clocks": clk,
+            "e2e": {"value": ws * p.nnz / e2e_t if e2e_t else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "step": "ntc_set_observed (pinned host COO, device bucketing) + ntc_epoch + "
+                            "ntc_get_factor x3"},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+                         "peak_kind": hbm_kind, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": ncu_traffic(kname),
+                         "alg_bytes_per_launch": bytes_per_launch, "ms_per_launch": per_launch_ms},
+            "roofline_epoch": {"alg_bytes_per_epoch": alg_bytes / args.steps,
+                               "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9 * ws,
+                               "frac_of_hbm": alg_bytes / (ms * 1e-3) / 1e9 / hbm, "peak_kind": hbm_kind},
+            "roofline_alu": {"kernel": "k_heavy_gram", "achieved": gram_tf, "peak": fp32_peak,
+                             "unit": "TFLOP/s", "frac": gram_tf / fp32_peak if fp32_peak else None,
+                             "peak_kind": "measured FP32 FMA microbenchmark, same run",
+                             "flops_per_visit": flops_per_visit},
+            "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                            "share": v["ms"] / total_k if total_k else None} for k, v in prof.items()},
+            "visits_per_s": ws * visits / (ms * 1e-3)}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        del g
+        torch.cuda.empty_cache()
+        line["cpu_baseline"], _ = cpu_baseline(p, steps=1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ntc(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -72,6 +72,8 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
  *   "chunk"          observations per thread block of a split row (default 16384)
  * Must be called before ntc_set_observed for "keep_perm".  Errors: NTC_ERR_ARG. */
 ntc_status ntc_set_param(ntc_handle* h, const char* key, double value);
+/* (also "profile": 1 brackets every mode-update kernel with CUDA events, see
+ * ntc_get_profile) */
 
 /* Enqueue all further work on this cudaStream_t (e.g. a PyTorch stream);
  * NULL selects the legacy default stream.  Errors: none besides NTC_ERR_ARG. */
@@ -146,6 +148,28 @@ typedef struct {
     int64_t kernel_launches;
 } ntc_stats;
 ntc_status ntc_get_stats(ntc_handle* h, ntc_stats* out);
+
+/* Per-kernel timing on the handle's stream.  With "profile" set to 1
+ * (ntc_set_param), every kernel launch of the mode update is bracketed by CUDA
+ * events.  ntc_get_profile synchronises the stream and returns, for kernel
+ * class `kind` (NTC_K_*), the summed event time in ms, the number of launches
+ * and the algorithmic bytes those launches moved by the model of the sampled
+ * visits (index, value and factor-row reads per visit; factor-row traffic per
+ * row update), then clears that class.  Errors: NTC_ERR_ARG for a bad kind. */
+enum {
+    NTC_K_LIGHT = 0,          /* fused sample + Gram + row update, one block per row */
+    NTC_K_HEAVY_SAMPLE = 1,   /* keys and certain/candidate split per chunk          */
+    NTC_K_HEAVY_RESOLVE = 2,  /* exact k-subset per split row                        */
+    NTC_K_HEAVY_GRAM = 3,     /* Gram/data partials per chunk                         */
+    NTC_K_HEAVY_FINISH = 4,   /* partial sums and row update per split row           */
+    NTC_K_COUNT = 5
+};
+ntc_status ntc_get_profile(ntc_handle* h, int kind, double* ms, int64_t* launches, int64_t* alg_bytes);
+
+/* Utility: FP32 fused multiply-add throughput of the current device in
+ * TFLOP/s, measured with a register-resident FMA kernel on `cuda_stream`
+ * (2 flops per FMA).  The roofline of the ALU-bound Gram work uses it. */
+ntc_status ntc_measure_fp32_peak(void* cuda_stream, double* tflops);
 
 /* Test hooks.  ntc_get_bucket: the mode's bucket (Sec. II-B rows of X_(i)):
  * row_ptr[dims[mode]+1] and, if keep_perm was set, perm[nnz] (bucket position

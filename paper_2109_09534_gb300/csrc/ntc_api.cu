@@ -90,6 +90,22 @@ struct ntc_handle {
     ModePlan plan[kMaxOrder];
     // scratch
     DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, stat, red, mask;
+    // per-kernel event timing ("profile")
+    int profile = 0;
+    struct Pending {
+        int kind;
+        int64_t bytes;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    double prof_ms[NTC_K_COUNT] = {};
+    int64_t prof_launches[NTC_K_COUNT] = {}, prof_bytes[NTC_K_COUNT] = {};
+    ~ntc_handle() {
+        for (auto& q : pending) {
+            cudaEventDestroy(q.a);
+            cudaEventDestroy(q.b);
+        }
+    }
 };
 
 namespace {
@@ -124,9 +140,35 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 // ---- mode update launches ---------------------------------------------------
+// Enqueues one kernel; with profiling on, brackets it with a pair of events.
+struct Launcher {
+    ntc_handle* h;
+    cudaStream_t s;
+    int64_t* launches;
+    int64_t bpv, bpr;   // algorithmic bytes per visit and per row update
+    template <class F>
+    cudaError_t run(int kind, int64_t bytes, F&& f) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (h->profile) {
+            cudaError_t e = cudaEventCreate(&a);
+            if (e == cudaSuccess) e = cudaEventCreate(&b);
+            if (e == cudaSuccess) e = cudaEventRecord(a, s);
+            if (e != cudaSuccess) return e;
+        }
+        f();
+        ++*launches;
+        if (h->profile) {
+            cudaError_t e = cudaEventRecord(b, s);
+            if (e != cudaSuccess) return e;
+            h->pending.push_back({kind, bytes, a, b});
+        }
+        return cudaSuccess;
+    }
+};
+
 template <int RP, int EW, bool BF>
-cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, cudaStream_t s, bool mask_only,
-                          int64_t* launches) {
+cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, bool mask_only) {
+    cudaStream_t s = L.s;
     static bool attr = false;
     if (!attr) {
         cudaError_t e;
@@ -135,42 +177,50 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, cudaStream_t s, 
         if ((e = set_smem(k_heavy_finish<RP>, heavy_finish_smem<RP>())) != cudaSuccess) return e;
         attr = true;
     }
+    cudaError_t e = cudaSuccess;
     if (p.n_light > 0) {
-        k_light<RP, EW, BF><<<p.n_light, kThreads, LightSmem<RP, EW, BF>::BYTES, s>>>(a);
-        ++*launches;
+        const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv + (int64_t)p.n_light * L.bpr;
+        e = L.run(NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
+            k_light<RP, EW, BF><<<p.n_light, kThreads, LightSmem<RP, EW, BF>::BYTES, s>>>(a);
+        });
+        if (e != cudaSuccess) return e;
     }
     if (p.n_heavy > 0) {
-        cudaError_t e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
+        e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
         if (e != cudaSuccess) return e;
-        k_heavy_sample<<<p.n_chunks, kThreads, 0, s>>>(a);
-        k_heavy_resolve<<<p.n_heavy, kThreads, 0, s>>>(a);
-        *launches += 2;
+        e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_heavy_sample<<<p.n_chunks, kThreads, 0, s>>>(a); });
+        if (e != cudaSuccess) return e;
+        e = L.run(NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<<<p.n_heavy, kThreads, 0, s>>>(a); });
+        if (e != cudaSuccess) return e;
         if (mask_only) {
             k_heavy_mask<<<p.n_chunks + p.n_heavy, kThreads, 0, s>>>(a);
-            ++*launches;
+            ++*L.launches;
         } else {
-            k_heavy_gram<RP, EW, BF><<<p.n_chunks + p.n_heavy, kThreads, heavy_gram_smem<RP, EW, BF>(), s>>>(a);
-            k_heavy_finish<RP><<<p.n_heavy, kThreads, heavy_finish_smem<RP>(), s>>>(a);
-            *launches += 2;
+            e = L.run(NTC_K_HEAVY_GRAM, p.visits_heavy * L.bpv, [&] {
+                k_heavy_gram<RP, EW, BF><<<p.n_chunks + p.n_heavy, kThreads, heavy_gram_smem<RP, EW, BF>(), s>>>(a);
+            });
+            if (e != cudaSuccess) return e;
+            e = L.run(NTC_K_HEAVY_FINISH, (int64_t)p.n_heavy * L.bpr, [&] {
+                k_heavy_finish<RP><<<p.n_heavy, kThreads, heavy_finish_smem<RP>(), s>>>(a);
+            });
+            if (e != cudaSuccess) return e;
         }
     }
     return cudaGetLastError();
 }
 
 template <int RP>
-cudaError_t launch_mode_rp(int ew, bool bf, const ModeArgs& a, const ModePlan& p, cudaStream_t s, bool mo,
-                           int64_t* l) {
-    if (ew == 4) return bf ? launch_mode_t<RP, 4, true>(a, p, s, mo, l) : launch_mode_t<RP, 4, false>(a, p, s, mo, l);
-    return bf ? launch_mode_t<RP, 8, true>(a, p, s, mo, l) : launch_mode_t<RP, 8, false>(a, p, s, mo, l);
+cudaError_t launch_mode_rp(int ew, bool bf, const ModeArgs& a, const ModePlan& p, Launcher& L, bool mo) {
+    if (ew == 4) return bf ? launch_mode_t<RP, 4, true>(a, p, L, mo) : launch_mode_t<RP, 4, false>(a, p, L, mo);
+    return bf ? launch_mode_t<RP, 8, true>(a, p, L, mo) : launch_mode_t<RP, 8, false>(a, p, L, mo);
 }
 
-cudaError_t launch_mode(int rp, int ew, bool bf, const ModeArgs& a, const ModePlan& p, cudaStream_t s, bool mo,
-                        int64_t* l) {
+cudaError_t launch_mode(int rp, int ew, bool bf, const ModeArgs& a, const ModePlan& p, Launcher& L, bool mo) {
     switch (rp) {
-        case 8: return launch_mode_rp<8>(ew, bf, a, p, s, mo, l);
-        case 16: return launch_mode_rp<16>(ew, bf, a, p, s, mo, l);
-        case 32: return launch_mode_rp<32>(ew, bf, a, p, s, mo, l);
-        default: return launch_mode_rp<64>(ew, bf, a, p, s, mo, l);
+        case 8: return launch_mode_rp<8>(ew, bf, a, p, L, mo);
+        case 16: return launch_mode_rp<16>(ew, bf, a, p, L, mo);
+        case 32: return launch_mode_rp<32>(ew, bf, a, p, L, mo);
+        default: return launch_mode_rp<64>(ew, bf, a, p, L, mo);
     }
 }
 
@@ -343,23 +393,35 @@ ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t a
     return a;
 }
 
+// Algorithmic bytes (the model of the sampled visits): per visit the other
+// modes' indices, the value and the other modes' factor rows; per row update
+// the row pointer, the master row read and written (plus the bfloat16 copy
+// and the extrapolation row when they exist).
+Launcher make_launcher(ntc_handle* h) {
+    const int64_t N = h->order, R = h->rank, sz = h->storage_bf16 ? 2 : 4;
+    Launcher L;
+    L.h = h;
+    L.s = h->stream;
+    L.launches = &h->stats.kernel_launches;
+    L.bpv = (N - 1) * 4 + 4 + (N - 1) * R * sz;
+    L.bpr = 8 + 4 * R + 4 * R + (h->storage_bf16 ? 2 * R : 0) + (h->max_inner > 1 ? 8 * R : 0);
+    return L;
+}
+
 // Algorithm 1 on one mode at AO iteration ao_iter.
 ntc_status run_snmc(ntc_handle* h, int mode, double c, uint64_t seed, uint64_t ao_iter) {
     ntc_status st = build_plan(h, mode, c);
     if (st != NTC_OK) return st;
     const ModePlan& p = h->plan[mode];
+    Launcher L = make_launcher(h);
     for (int l = 0; l < h->max_inner; ++l) {
         ModeArgs a = mode_args(h, mode, l, seed, ao_iter);
-        NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, p, h->stream, false,
-                                &h->stats.kernel_launches));
+        NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, p, L, false));
         h->stats.visits += p.visits;
         h->stats.visits_heavy += p.visits_heavy;
         h->stats.rows_updated += p.rows_updated;
         h->stats.rows_skipped += p.rows_skipped;
-        const int64_t N = h->order, R = h->rank, s = h->storage_bf16 ? 2 : 4;
-        h->stats.alg_bytes += p.visits * ((N - 1) * 4 + 4 + (N - 1) * R * s) +
-                              p.rows_updated * (8 + 4 * R + 4 * R + (h->storage_bf16 ? 2 * R : 0) +
-                                                (h->max_inner > 1 ? 8 * R : 0));
+        h->stats.alg_bytes += p.visits * L.bpv + p.rows_updated * L.bpr;
     }
     return NTC_OK;
 }
@@ -569,6 +631,8 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
     } else if (k == "init_seed") {
         if (!(v >= 0)) return fail(h, NTC_ERR_ARG, "init_seed must be >= 0");
         h->init_seed = (uint64_t)v;
+    } else if (k == "profile") {
+        h->profile = v != 0.0;
     } else if (k == "keep_perm") {
         h->keep_perm = v != 0.0;
     } else if (k == "bracket_z") {
@@ -815,10 +879,35 @@ ntc_status ntc_sample_mask(ntc_handle* h, int mode, double c, uint64_t seed, uin
     NTC_CUDA(h, cudaMemsetAsync(h->mask.p, 0, (size_t)std::max<int64_t>(h->nnz, 1), h->stream));
     ModeArgs a = mode_args(h, mode, inner, seed, ao_iter);
     a.mask_out = h->mask.as<uint8_t>();
-    NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, h->plan[mode], h->stream, true,
-                            &h->stats.kernel_launches));
+    Launcher L = make_launcher(h);
+    NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, h->plan[mode], L, true));
     NTC_CUDA(h, cudaMemcpyAsync(mask, h->mask.p, (size_t)h->nnz, cudaMemcpyDeviceToHost, h->stream));
     NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return NTC_OK;
+}
+
+ntc_status ntc_get_profile(ntc_handle* h, int kind, double* ms, int64_t* launches, int64_t* alg_bytes) {
+    if (!h || kind < 0 || kind >= NTC_K_COUNT) return NTC_ERR_ARG;
+    h->err.clear();
+    if (!h->pending.empty()) {
+        NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (auto& q : h->pending) {
+            float t = 0.f;
+            NTC_CUDA(h, cudaEventElapsedTime(&t, q.a, q.b));
+            h->prof_ms[q.kind] += t;
+            h->prof_launches[q.kind] += 1;
+            h->prof_bytes[q.kind] += q.bytes;
+            cudaEventDestroy(q.a);
+            cudaEventDestroy(q.b);
+        }
+        h->pending.clear();
+    }
+    if (ms) *ms = h->prof_ms[kind];
+    if (launches) *launches = h->prof_launches[kind];
+    if (alg_bytes) *alg_bytes = h->prof_bytes[kind];
+    h->prof_ms[kind] = 0.0;
+    h->prof_launches[kind] = 0;
+    h->prof_bytes[kind] = 0;
     return NTC_OK;
 }
 

@@ -21,6 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ntc.h")
 
 NTC_OK, NTC_ERR_ARG, NTC_ERR_INDEX, NTC_ERR_OOM, NTC_ERR_STATE, NTC_ERR_CUDA = range(6)
+KERNELS = ["light", "heavy_sample", "heavy_resolve", "heavy_gram", "heavy_finish"]
 _STATUS = {0: "NTC_OK", 1: "NTC_ERR_ARG", 2: "NTC_ERR_INDEX", 3: "NTC_ERR_OOM", 4: "NTC_ERR_STATE",
            5: "NTC_ERR_CUDA"}
 
@@ -79,6 +80,8 @@ def load(path: Optional[str] = None):
         "ntc_get_stats": [P, ctypes.POINTER(ntc_stats)],
         "ntc_get_bucket": [P, i32, P, P],
         "ntc_sample_mask": [P, i32, dbl, u64, u64, i32, P],
+        "ntc_get_profile": [P, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "ntc_measure_fp32_peak": [P, ctypes.POINTER(dbl)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -100,6 +103,13 @@ def _check(h, status: int) -> None:
     if status != NTC_OK:
         msg = load().ntc_last_error(h) if h else b""
         raise NTCError(status, (msg or b"").decode())
+
+
+def measure_fp32_peak(stream: int = 0) -> float:
+    """FP32 FMA throughput of the current device, TFLOP/s."""
+    out = ctypes.c_double()
+    _check(None, load().ntc_measure_fp32_peak(ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out.value
 
 
 class NTC:
@@ -212,11 +222,19 @@ class NTC:
         _check(self.h, self.L.ntc_get_stats(self.h, ctypes.byref(s)))
         return {k: int(getattr(s, k)) for k, _ in ntc_stats._fields_}
 
+    def profile(self) -> dict:
+        """Per kernel class: summed event ms, launches, algorithmic bytes (then cleared)."""
+        out = {}
+        for kind, name in enumerate(KERNELS):
+            ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+            _check(self.h, self.L.ntc_get_profile(self.h, kind, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+            out[name] = dict(ms=ms.value, launches=int(n.value), alg_bytes=int(b.value))
+        return out
+
     def get_bucket(self, mode: int, perm: bool = False):
         rp = np.zeros(self.dims[mode] + 1, dtype=np.int64)
         pm = None
         if perm:
-            nnz = None
             pm = np.zeros(max(self._nnz_hint(rp, mode), 1), dtype=np.int64)
         _check(self.h, self.L.ntc_get_bucket(self.h, int(mode), _ptr(rp), _ptr(pm) if pm is not None else None))
         if pm is not None:
