@@ -180,6 +180,24 @@ ntc_status ntc_get_bucket(ntc_handle* h, int mode, int64_t* row_ptr, int64_t* pe
 ntc_status ntc_sample_mask(ntc_handle* h, int mode, double c, uint64_t seed, uint64_t ao_iter,
                            int inner, uint8_t* mask);
 
+/* RMSE without allocating: the paper has no counterpart; this exists for
+ * callers that cannot allocate device memory while they run -- a serving
+ * process whose HBM is handed out up front to resident jobs, or a framework
+ * whose caching allocator owns the device memory and must not see the
+ * device-wide synchronisation that cudaMalloc/cudaFree can bring.  Same result
+ * as ntc_rmse, but idx_dev[n][order] (int32) and vals_dev[n] (float32) are
+ * DEVICE pointers on the handle's device, which must be current; the indices
+ * are not checked.  *out (host) receives the RMSE; the call synchronises the
+ * handle's stream.  It calls no cudaMalloc/cudaFree: its scratch is a fixed
+ * 32 KB array in the library's device memory, one double per block of 2048
+ * queries, so n may be at most 4096 * 2048 = 8,388,608 (larger n returns
+ * NTC_ERR_ARG).  The first call on a device looks up that array's address,
+ * so make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (other streams, other threads, other
+ * handles on the same device) race and must be serialised by the caller.
+ * Errors: NTC_ERR_ARG, NTC_ERR_STATE (handle's device not current), NTC_ERR_CUDA. */
+ntc_status ntc_rmse_noalloc(ntc_handle* h, int64_t n, const int32_t* idx_dev, const float* vals_dev, double* out);
+
 /* Message for the last failed call on h ("" if none); valid until the next call. */
 const char* ntc_last_error(const ntc_handle* h);
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -568,6 +569,34 @@ FactorSet factor_set(ntc_handle* h) {
 
 }  // namespace
 
+// ---- allocation-free RMSE -----------------------------------------------------
+// One double of partial sum per block of kNoAllocPerBlock queries, plus the
+// final sum, in a file-scope device array: every GPU that loads the library
+// holds these 32 KB until the process exits, and every call shares them.
+constexpr int kNoAllocPerBlock = 2048;
+constexpr int kNoAllocMaxBlocks = 4096;
+constexpr int64_t kNoAllocMaxQueries = (int64_t)kNoAllocPerBlock * kNoAllocMaxBlocks;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 1];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::once_flag g_noalloc_once[kNoAllocMaxDevices];
+cudaError_t g_noalloc_err[kNoAllocMaxDevices];
+double* g_noalloc_ptr[kNoAllocMaxDevices];
+
+// Device address of the scratch array for the current device, looked up once
+// per device.  The array's name in host code is only a host-side stand-in.
+cudaError_t noalloc_scratch(int dev, double** out) {
+    std::call_once(g_noalloc_once[dev], [dev] {
+        void* p = nullptr;
+        g_noalloc_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    });
+    *out = g_noalloc_ptr[dev];
+    return g_noalloc_err[dev];
+}
+}  // namespace
+
 extern "C" {
 
 ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, ntc_handle** out) {
@@ -908,6 +937,35 @@ ntc_status ntc_get_profile(ntc_handle* h, int kind, double* ms, int64_t* launche
     h->prof_ms[kind] = 0.0;
     h->prof_launches[kind] = 0;
     h->prof_bytes[kind] = 0;
+    return NTC_OK;
+}
+
+ntc_status ntc_rmse_noalloc(ntc_handle* h, int64_t n, const int32_t* idx_dev, const float* vals_dev, double* out) {
+    if (!h || !out || n < 0 || (n > 0 && (!idx_dev || !vals_dev))) return NTC_ERR_ARG;
+    h->err.clear();
+    if (n > kNoAllocMaxQueries)
+        return fail(h, NTC_ERR_ARG, "ntc_rmse_noalloc: n = " + std::to_string(n) + " exceeds the limit of " +
+                                        std::to_string(kNoAllocMaxQueries) + " queries per call");
+    if (n == 0) {
+        *out = 0.0;
+        return NTC_OK;
+    }
+    int dev = -1;
+    NTC_CUDA(h, cudaGetDevice(&dev));
+    if (dev != h->device) return fail(h, NTC_ERR_STATE, "ntc_rmse_noalloc: the handle's device is not current");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(h, NTC_ERR_ARG, "ntc_rmse_noalloc: device id too large");
+    double* scratch = nullptr;
+    NTC_CUDA(h, noalloc_scratch(dev, &scratch));
+    const int nb = (int)((n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+    // every partial slot 0..nb-1 is written before it is read, and the final
+    // slot is written by the second kernel, so nothing needs clearing
+    k_sq_resid<<<nb, kThreads, 0, h->stream>>>(factor_set(h), idx_dev, vals_dev, n, scratch);
+    k_sum_partials<<<1, kThreads, 0, h->stream>>>(scratch, nb, scratch + kNoAllocMaxBlocks);
+    NTC_CUDA(h, cudaGetLastError());
+    double s = 0.0;
+    NTC_CUDA(h, cudaMemcpyAsync(&s, scratch + kNoAllocMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    *out = std::sqrt(s / (double)n);
     return NTC_OK;
 }
 
