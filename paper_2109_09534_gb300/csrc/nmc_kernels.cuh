@@ -74,31 +74,77 @@ __device__ unsigned long long block_select_kth(const Get& get, int n, int k, uns
 }
 
 // ---------------------------------------------------------------------------
-// Gram / data reduction over a list of sampled observations of one row:
+// 16-byte asynchronous global -> shared copies (cp.async, L1 bypassed).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// Same, cached in L1 as well: factor rows are re-read often (skewed indices
+// make a few rows very hot), and L1 absorbs those repeats.
+__device__ __forceinline__ void cp_async16_ca(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Gram / data reduction over the sampled observations of one row (or one
+// chunk of a row):
 //   G = sum_e k_e k_e^T  (upper triangle),  b = sum_e x_e k_e
 // k_e is the Khatri-Rao row of observation e (Hadamard product of the other
 // modes' factor rows, Sec. II unfolding with K of Sec. III), so that
 // H_{l,p} = G + lambda I (Alg. 1 line 9) and W_l(p,:) = -b (line 6).
-// Threads own 8x8 tiles (a, b), a <= b, of G; NG groups of NP threads take
-// interleaved visits of each staged tile of VT gathered rows.
+//
+// Per staged tile of VT visits: bucket entries (other-mode indices and the
+// value) and then the other modes' factor rows are copied to shared memory
+// with cp.async; a product pass forms each k_e once (and accumulates b), and
+// the FMA pass adds k_e k_e^T into 8x8 register tiles (a, b), a <= b, owned by
+// NP threads, NG groups of which take interleaved visits.  Iteration t runs
+// the FMA pass of tile t and the product pass of tile t+1 while the factor
+// rows of tiles t+2, t+3 and the entries of tiles t+4, t+5 are in flight and
+// the bucket positions of tile t+6 are loaded into registers.
 template <int RP, int EW, bool BF16>
 struct Gram {
     static constexpr int T = RP / 8;
     static constexpr int NP = T * (T + 1) / 2;
     static constexpr int NG = kThreads / NP;
     static constexpr int NACT = NG * NP;
-    static constexpr int VPG = (96 + NG - 1) / NG;
-    static constexpr int VT = NG * VPG;           // visits per staged tile
-    static constexpr int QPV = RP / 4;            // float4 per k row
-    static constexpr int KST = RP + 4;            // staged row stride (floats)
-    static constexpr int PW = NP * 72;            // reduced floats: 64 tile + 8 of b per pair
-    // shared memory (floats)
-    static constexpr int SM_TILE = VT * KST + VT;
-    static constexpr int SM_RED = NACT * 72;
-    static constexpr int SM_SUM = PW;
+    static constexpr int ES = BF16 ? 2 : 4;           // bytes per stored factor element
+    static constexpr int ROWB = RP * ES;              // bytes per factor row
+    static constexpr int RST = ROWB + 16;             // staged row stride (bank spread)
+    static constexpr int CPR = ROWB / 16;             // 16-byte copies per row
+    static constexpr int QPV = RP / 4;                // float4 per k row
+    static constexpr int KST = RP + 4;                // k-tile row stride (floats)
+    static constexpr int NOMAX = EW == 4 ? 3 : 7;     // other modes
+    static constexpr int ENTB = EW * 4;               // bytes per bucket entry
+    static constexpr int SR = 3;                      // factor-row stages
+    static constexpr int SE = 5;                      // entry stages
+    static constexpr int NOTYP = EW == 4 ? 2 : 4;     // other modes the tile size is tuned for
+    static constexpr int BPV_TYP = SR * NOTYP * RST + SE * ENTB + 2 * KST * 4;
+    static constexpr int BPV_MAX = SR * NOMAX * RST + SE * ENTB + 2 * KST * 4;
+    static constexpr int VT_BUDGET = 100000 / BPV_TYP;
+    static constexpr int VT_MAX = 200000 / BPV_MAX;
+    static constexpr int VT0 = VT_BUDGET < VT_MAX ? VT_BUDGET : VT_MAX;
+    static constexpr int VT1 = VT0 >= NG ? (VT0 / NG) * NG : VT0;
+    static constexpr int VT = VT1 > 256 ? 256 : (VT1 < 1 ? 1 : VT1);   // visits per staged tile
+    static constexpr int VPG = (VT + NG - 1) / NG;    // visits per group per tile
+    static constexpr int PW = NP * 64 + RP;           // reduced floats: the tiles, then b
+    static constexpr int RED_BYTES = (NACT * 64 + kThreads * 4) * 4;
+    static_assert(kThreads % QPV == 0, "a thread's product-pass quad must be fixed");
+
+    __host__ __device__ static constexpr size_t pipe_bytes(int no) {
+        return (size_t)SR * no * VT * RST + (size_t)SE * VT * ENTB + (size_t)2 * VT * KST * 4;
+    }
+    __host__ __device__ static constexpr size_t region_bytes(int no) {
+        return pipe_bytes(no) > (size_t)RED_BYTES ? pipe_bytes(no) : (size_t)RED_BYTES;
+    }
 
     float acc[8][8];
-    float bacc[8];
+    float4 bq;       // b partial of this thread's product-pass quad
     int g, pa, pb;
     bool active;
 
@@ -117,50 +163,48 @@ struct Gram {
             }
             p -= T - a;
         }
+        bq = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            bacc[i] = 0.f;
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-        }
     }
 
-    // Gather the Khatri-Rao rows of visits [v0, v0 + nv) into the staged tile.
-    template <class GetPos>
-    __device__ __forceinline__ void gather(const ModeArgs& a, const GetPos& getpos, int v0, int nv,
-                                           float* tile) {
-        const Entry<EW>* bucket = reinterpret_cast<const Entry<EW>*>(a.bucket);
-        float* xt = tile + VT * KST;
+    __device__ __forceinline__ static float4 load4(const unsigned char* row, int q) {
+        if (BF16) return bf16x4_to_f32(*reinterpret_cast<const uint2*>(row + q * 8));
+        return *reinterpret_cast<const float4*>(row + q * 16);
+    }
+
+    // k rows of tile visits [0, nv) into the k-tile; b += x k.
+    __device__ __forceinline__ void product(const unsigned char* rows, const Entry<EW>* ents, float* kt, int nv,
+                                            int no) {
+        const int q = threadIdx.x % QPV;
         for (int s = threadIdx.x; s < nv * QPV; s += kThreads) {
-            const int v = s / QPV, qd = s - v * QPV;
-            const uint32_t pos = getpos(v0 + v);
-            const Entry<EW> e = bucket[pos];
-            float4 prod = make_float4(1.f, 1.f, 1.f, 1.f);
-            for (int o = 0; o < a.n_other; ++o) {
-                const size_t off = (size_t)e.w[o] * RP + 4 * qd;
-                float4 u;
-                if (BF16) {
-                    const uint2 raw = *reinterpret_cast<const uint2*>(
-                        static_cast<const uint16_t*>(a.other[o]) + off);
-                    u = bf16x4_to_f32(raw);
-                } else {
-                    u = *reinterpret_cast<const float4*>(static_cast<const float*>(a.other[o]) + off);
-                }
-                prod.x *= u.x;
-                prod.y *= u.y;
-                prod.z *= u.z;
-                prod.w *= u.w;
+            const int v = s / QPV;
+            float4 p = load4(rows + (size_t)v * RST, q);
+            for (int o = 1; o < no; ++o) {
+                const float4 u = load4(rows + ((size_t)o * VT + v) * RST, q);
+                p.x *= u.x;
+                p.y *= u.y;
+                p.z *= u.z;
+                p.w *= u.w;
             }
-            *reinterpret_cast<float4*>(tile + v * KST + 4 * qd) = prod;
-            if (qd == 0) xt[v] = __int_as_float(e.w[EW - 1]);
+            *reinterpret_cast<float4*>(kt + v * KST + 4 * q) = p;
+            const float x = __int_as_float(ents[v].w[EW - 1]);
+            bq.x = fmaf(x, p.x, bq.x);
+            bq.y = fmaf(x, p.y, bq.y);
+            bq.z = fmaf(x, p.z, bq.z);
+            bq.w = fmaf(x, p.w, bq.w);
         }
     }
 
-    __device__ __forceinline__ void accumulate(const float* tile, int nv) {
+    __device__ __forceinline__ void accumulate(const float* kt, int nv) {
         if (!active) return;
-        const float* xt = tile + VT * KST;
-        for (int v = g; v < nv; v += NG) {
-            const float* kv = tile + v * KST;
+#pragma unroll
+        for (int j = 0; j < VPG; ++j) {
+            const int v = g + j * NG;
+            if (v >= nv) break;
+            const float* kv = kt + v * KST;
             const float4 a0 = *reinterpret_cast<const float4*>(kv + 8 * pa);
             const float4 a1 = *reinterpret_cast<const float4*>(kv + 8 * pa + 4);
             const float4 b0 = *reinterpret_cast<const float4*>(kv + 8 * pb);
@@ -170,43 +214,117 @@ struct Gram {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-            if (pa == pb) {
-                const float x = xt[v];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) bacc[i] = fmaf(x, av[i], bacc[i]);
-            }
+                for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(av[i], bv[jj], acc[i][jj]);
         }
     }
 
-    // Whole list: staged tiles of VT visits.
+    // All nvis visits; getpos(i) is the bucket position of visit i.  `pipe`
+    // holds region_bytes(no) bytes of shared memory.
     template <class GetPos>
-    __device__ __forceinline__ void run(const ModeArgs& a, const GetPos& getpos, int nvis, float* tile) {
-        for (int v0 = 0; v0 < nvis; v0 += VT) {
-            const int nv = min(VT, nvis - v0);
-            gather(a, getpos, v0, nv, tile);
+    __device__ __forceinline__ void run(const ModeArgs& a, const GetPos& getpos, int nvis, unsigned char* pipe) {
+        const int no = a.n_other;
+        const int tid = threadIdx.x;
+        const size_t stage_rows = (size_t)no * VT * RST;
+        unsigned char* rows = pipe;                                                       // [SR][no][VT][RST]
+        Entry<EW>* ents = reinterpret_cast<Entry<EW>*>(pipe + SR * stage_rows);          // [SE][VT]
+        float* ktile = reinterpret_cast<float*>(pipe + SR * stage_rows + (size_t)SE * VT * ENTB);  // [2][VT][KST]
+        const Entry<EW>* bucket = reinterpret_cast<const Entry<EW>*>(a.bucket);
+        const int ntiles = (nvis + VT - 1) / VT;
+        auto tile_n = [&](int t) { return min(VT, nvis - t * VT); };
+        auto pos_of = [&](int t) -> uint32_t {
+            return (t < ntiles && tid < tile_n(t)) ? getpos(t * VT + tid) : 0u;
+        };
+        auto issue_entries = [&](int t, uint32_t pos) {
+            if (t < ntiles && tid < tile_n(t)) {
+                const unsigned char* src = reinterpret_cast<const unsigned char*>(bucket + pos);
+                unsigned char* dst = reinterpret_cast<unsigned char*>(ents + (t % SE) * VT + tid);
+#pragma unroll
+                for (int c = 0; c < ENTB / 16; ++c) cp_async16(dst + 16 * c, src + 16 * c);
+            }
+        };
+        auto issue_rows = [&](int t) {
+            if (t >= ntiles) return;
+            const int nv = tile_n(t);
+            const Entry<EW>* e = ents + (t % SE) * VT;
+            unsigned char* r = rows + (size_t)(t % SR) * stage_rows;
+            // copy i = (o * VT + v) * CPR + c; VT and CPR are compile-time constants
+            const int total = no * VT * CPR;
+            for (int i = tid; i < total; i += kThreads) {
+                const int c = i % CPR;
+                const int vo = i / CPR;
+                const int v = vo % VT;
+                const int o = vo / VT;
+                if (v >= nv) continue;
+                const unsigned char* src = static_cast<const unsigned char*>(a.other[o]) +
+                                           (size_t)e[v].w[o] * ROWB + 16 * c;
+                cp_async16_ca(r + (size_t)vo * RST + 16 * c, src);
+            }
+        };
+        auto do_product = [&](int t) {
+            if (t < ntiles)
+                product(rows + (size_t)(t % SR) * stage_rows, ents + (t % SE) * VT, ktile + (t & 1) * VT * KST,
+                        tile_n(t), no);
+        };
+        // prologue: k-tile 0 formed; rows 1, 2 and entries 3, 4 in flight;
+        // the position of tile 5 in a register
+        issue_entries(0, pos_of(0));
+        issue_entries(1, pos_of(1));
+        issue_entries(2, pos_of(2));
+        cp_async_commit();
+        uint32_t p3 = pos_of(3), p4 = pos_of(4);
+        cp_async_wait<0>();
+        __syncthreads();
+        issue_rows(0);
+        issue_rows(1);
+        issue_entries(3, p3);
+        cp_async_commit();
+        issue_rows(2);
+        issue_entries(4, p4);
+        cp_async_commit();
+        uint32_t pos_next = pos_of(5);
+        cp_async_wait<1>();
+        __syncthreads();
+        do_product(0);
+        for (int t = 0; t < ntiles; ++t) {
+            cp_async_wait<1>();      // rows of t+1, entries of t+3
             __syncthreads();
-            accumulate(tile, nv);
+            do_product(t + 1);
+            issue_rows(t + 3);
+            issue_entries(t + 5, pos_next);
+            pos_next = pos_of(t + 6);
+            cp_async_commit();
+            accumulate(ktile + (t & 1) * VT * KST, tile_n(t));
             __syncthreads();
         }
+        cp_async_wait<0>();
+        __syncthreads();
     }
 
-    // Fixed-order reduction over the NG groups into sum[PW] (shared).
+    // Fixed-order reduction over the NG groups (tiles) and over the threads of
+    // each product quad (b) into sum[PW] (shared); `red` may alias `pipe`.
+    // The buffer is slot-major (red[slot * NACT + thread]) so that a warp's
+    // stores fall in consecutive banks.
     __device__ __forceinline__ void reduce(float* red, float* sum) {
         if (active) {
-            float* r = red + (size_t)threadIdx.x * 72;
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) r[i * 8 + j] = acc[i][j];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) r[64 + i] = bacc[i];
+                for (int j = 0; j < 8; ++j) red[(i * 8 + j) * NACT + threadIdx.x] = acc[i][j];
         }
+        reinterpret_cast<float4*>(red + NACT * 64)[threadIdx.x] = bq;
         __syncthreads();
-        for (int s = threadIdx.x; s < PW; s += kThreads) {
+        for (int s = threadIdx.x; s < NP * 64; s += kThreads) {
+            const int p = s >> 6, ij = s & 63;
+            const float* col = red + ij * NACT + p;
             float t = 0.f;
-            for (int gg = 0; gg < NG; ++gg) t += red[(size_t)gg * PW + s];
+            for (int gg = 0; gg < NG; ++gg) t += col[gg * NP];
             sum[s] = t;
+        }
+        for (int r = threadIdx.x; r < RP; r += kThreads) {
+            const int q = r / 4, c = r % 4;
+            float t = 0.f;
+            for (int th = q; th < kThreads; th += QPV) t += red[NACT * 64 + th * 4 + c];
+            sum[NP * 64 + r] = t;
         }
         __syncthreads();
     }
@@ -237,16 +355,11 @@ __device__ __forceinline__ void build_H(const float* sum, float* H, float* bvec,
         pair_ab(T, p, &a, &b);
         const int r = 8 * a + i, c = 8 * b + j;
         if (a == b && i > j) continue;
-        const float v = sum[p * 72 + ij];
+        const float v = sum[p * 64 + ij];
         H[r * (RP + 1) + c] = v;
         H[c * (RP + 1) + r] = v;
     }
-    for (int s = threadIdx.x; s < NP * 8; s += kThreads) {
-        const int p = s >> 3, i = s & 7;
-        int a, b;
-        pair_ab(T, p, &a, &b);
-        if (a == b) bvec[8 * a + i] = sum[p * 72 + 64 + i];
-    }
+    for (int r = threadIdx.x; r < RP; r += kThreads) bvec[r] = sum[NP * 64 + r];
     __syncthreads();
     if (threadIdx.x < R) H[threadIdx.x * (RP + 1) + threadIdx.x] += lambda;
     __syncthreads();
@@ -261,6 +374,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Alg. 1 lines 8 and 10-13 for row p, run by warp 0: gradient H y - b
 // (= W + Z + lambda y), L_p by the power method (v0 = ones/sqrt(R), fixed
 // iteration count, Rayleigh quotient), projected step, momentum, extrapolation.
+// H is zero outside the leading R x R block, so loops run over RP.
 template <int RP>
 __device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float* H, const float* bvec,
                                            float* vsh) {
@@ -278,6 +392,19 @@ __device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float
         y[t] = in ? (a.read_y ? a.Y[base + r] : al[t]) : 0.f;
         v[t] = in ? 1.0f / sqrtf((float)R) : 0.f;
     }
+    auto matvec = [&](const float* x, float* out) {
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int r = lane + 32 * t;
+            float s = 0.f;
+            if (r < RP) {
+                const float* hr = H + r * (RP + 1);
+#pragma unroll
+                for (int c = 0; c < RP; ++c) s = fmaf(hr[c], x[c], s);
+            }
+            out[t] = s;
+        }
+    };
     // gradient: (H y)_r - b_r
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
@@ -285,15 +412,11 @@ __device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float
         if (r < RP) vsh[r] = y[t];
     }
     __syncwarp();
+    matvec(vsh, grad);
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
         const int r = lane + 32 * t;
-        float s = 0.f;
-        if (r < R) {
-            for (int c = 0; c < R; ++c) s = fmaf(H[r * (RP + 1) + c], vsh[c], s);
-            s -= bvec[r];
-        }
-        grad[t] = s;
+        grad[t] = r < R ? grad[t] - bvec[r] : 0.f;
     }
     __syncwarp();
     // power method
@@ -305,20 +428,19 @@ __device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float
             if (r < RP) vsh[r] = v[t];
         }
         __syncwarp();
+        matvec(vsh, w);
+        __syncwarp();
         float vw = 0.f, ww = 0.f;
 #pragma unroll
         for (int t = 0; t < PER; ++t) {
-            const int r = lane + 32 * t;
-            float s = 0.f;
-            if (r < R)
-                for (int c = 0; c < R; ++c) s = fmaf(H[r * (RP + 1) + c], vsh[c], s);
-            w[t] = s;
-            vw = fmaf(v[t], s, vw);
-            ww = fmaf(s, s, ww);
+            vw = fmaf(v[t], w[t], vw);
+            ww = fmaf(w[t], w[t], ww);
         }
-        __syncwarp();
-        vw = warp_sum(vw);
-        ww = warp_sum(ww);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vw += __shfl_xor_sync(0xffffffffu, vw, o);
+            ww += __shfl_xor_sync(0xffffffffu, ww, o);
+        }
         mu = vw;
         if (!(ww > 0.f)) {
             mu = 0.f;
@@ -347,29 +469,32 @@ __device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float
 // ---------------------------------------------------------------------------
 // Light rows (n_p <= kLightMax): one block per row does everything: keys in
 // shared memory, exact k-subset selection, Gram/data reduction, row update.
+// Shared memory: [visit list u16 x kLightMax | union(keys, Gram pipeline,
+// reduction)] + reduced sums, H, b, vectors, histogram.
 template <int RP, int EW, bool BF16>
 struct LightSmem {
     using G = Gram<RP, EW, BF16>;
-    // region A: selection (keys + visit list) and gather tile, later the reduction buffer
-    static constexpr int A_SEL = kLightMax + kLightMax / 2;   // keys (u32) + visits (u16), in floats
-    static constexpr int A_FLOATS = (A_SEL + G::SM_TILE) > G::SM_RED ? (A_SEL + G::SM_TILE) : G::SM_RED;
-    static constexpr int B_FLOATS = G::SM_SUM + RP * (RP + 1) + 2 * RP + 8;
-    static constexpr int MISC_U32 = 256 + 8 + 16;
-    static constexpr size_t BYTES = (size_t)(A_FLOATS + B_FLOATS + MISC_U32) * 4;
+    static constexpr size_t VIS = kLightMax * 2;
+    static constexpr size_t KEYS = kLightMax * 4;
+    __host__ __device__ static constexpr size_t union_bytes(int no) {
+        return G::region_bytes(no) > KEYS ? G::region_bytes(no) : KEYS;
+    }
+    static constexpr size_t TAIL = (size_t)(G::PW + RP * (RP + 1) + 2 * RP + 8 + 256 + 8 + 16) * 4;
+    __host__ __device__ static constexpr size_t bytes(int no) { return VIS + union_bytes(no) + TAIL; }
 };
 
 template <int RP, int EW, bool BF16>
 __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
     using G = Gram<RP, EW, BF16>;
     using S = LightSmem<RP, EW, BF16>;
-    extern __shared__ __align__(16) float smem[];
-    float* regA = smem;
-    uint32_t* keys = reinterpret_cast<uint32_t*>(regA);
-    uint16_t* vis = reinterpret_cast<uint16_t*>(regA + kLightMax);
-    float* tile = regA + S::A_SEL;
-    float* red = regA;
-    float* sum = smem + S::A_FLOATS;
-    float* H = sum + G::SM_SUM;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int no = a.n_other;
+    uint16_t* vis = reinterpret_cast<uint16_t*>(smem_raw);
+    unsigned char* uni = smem_raw + S::VIS;
+    uint32_t* keys = reinterpret_cast<uint32_t*>(uni);
+    float* red = reinterpret_cast<float*>(uni);
+    float* sum = reinterpret_cast<float*>(uni + S::union_bytes(no));
+    float* H = sum + G::PW;
     float* bvec = H + RP * (RP + 1);
     float* vsh = bvec + RP;
     unsigned* hist = reinterpret_cast<unsigned*>(vsh + RP + 8);
@@ -409,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
     G gr;
     gr.init();
     auto getpos = [&](int v) -> uint32_t { return uq0 + vis[v]; };
-    gr.run(a, getpos, nsel, tile);
+    gr.run(a, getpos, nsel, uni);
     gr.reduce(red, sum);
     build_H<RP>(sum, H, bvec, a.rank, a.lambda);
     finish_row<RP>(a, row, H, bvec, vsh);
@@ -417,8 +542,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
 
 // ---------------------------------------------------------------------------
 // Heavy rows, step 1: per chunk of a row, keys of every position; positions
-// with key < lo are certainly in the sample (written in position order);
-// lo <= key < hi are candidates whose fate depends on the whole row.
+// with key < lo are certainly in the sample and are written, in position
+// order; lo <= key < hi are
+// candidates whose fate depends on the whole row.  Each thread takes 8
+// consecutive positions per round, so one block scan serves 2048 positions.
+constexpr int kSamplePer = 8;
+
+template <int EW>
 __global__ void __launch_bounds__(kThreads) k_heavy_sample(ModeArgs a) {
     __shared__ int scan_tmp[kThreads / 32 + 1];
     const int ch = blockIdx.x;
@@ -430,20 +560,34 @@ __global__ void __launch_bounds__(kThreads) k_heavy_sample(ModeArgs a) {
     const longlong2 br = a.heavy_bracket[h];
     const unsigned long long lo = (unsigned long long)br.x, hi = (unsigned long long)br.y;
     int nsel = 0, ncand = 0;
-    for (uint32_t base = pb; base < pe; base += kThreads) {
-        const uint32_t q = base + threadIdx.x;
-        bool d = false, cn = false;
-        unsigned long long key = 0;
-        if (q < pe) {
-            key = a.ss.key(q);
-            d = key < lo;
-            cn = !d && key < hi;
+    for (uint32_t base = pb; base < pe; base += kThreads * kSamplePer) {
+        const uint32_t q0 = base + threadIdx.x * kSamplePer;
+        uint32_t key[kSamplePer];
+        int nd = 0, nc = 0;
+#pragma unroll
+        for (int j = 0; j < kSamplePer; ++j) {
+            const uint32_t q = q0 + j;
+            key[j] = q < pe ? a.ss.key(q) : 0xFFFFFFFFu;
+            const bool d = q < pe && key[j] < lo;
+            const bool cn = q < pe && !d && key[j] < hi;
+            nd += d;
+            nc += cn;
         }
         int tot;
-        const int packed = block_exclusive_scan((d ? 1 : 0) | (cn ? 0x10000 : 0), scan_tmp, &tot);
-        const int od = packed & 0xFFFF, oc = packed >> 16;
-        if (d) a.vis[pb + nsel + od] = q;
-        if (cn && ncand + oc < cap) a.cand[cand_off + ncand + oc] = (key << 32) | q;
+        const int packed = block_exclusive_scan(nd | (nc << 16), scan_tmp, &tot);
+        int od = nsel + (packed & 0xFFFF), oc = ncand + (packed >> 16);
+#pragma unroll
+        for (int j = 0; j < kSamplePer; ++j) {
+            const uint32_t q = q0 + j;
+            if (q >= pe) break;
+            const unsigned long long kk = key[j];
+            if (kk < lo) {
+                a.vis[pb + od++] = q;
+            } else if (kk < hi) {
+                if (oc < cap) a.cand[cand_off + oc] = (kk << 32) | q;
+                ++oc;
+            }
+        }
         nsel += tot & 0xFFFF;
         ncand += tot >> 16;
     }
@@ -460,6 +604,7 @@ __global__ void __launch_bounds__(kThreads) k_heavy_sample(ModeArgs a) {
 // smallest candidates give the exact k-subset.  If the bracket missed (too
 // few or too many candidates, or overflow), the row is reselected exactly from
 // recomputed keys and its chunk lists are rewritten.
+template <int EW>
 __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
     __shared__ unsigned hist[256 + 8];
     __shared__ int scan_tmp[kThreads / 32 + 1];
@@ -504,13 +649,20 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
         // the whole region is the m-th smallest real candidate
         const unsigned long long T = block_select_kth(get, ccap, m, hist);
         int ne = 0;
-        for (int base = 0; base < ccap; base += kThreads) {
-            const int j = base + threadIdx.x;
-            const unsigned long long cv = j < ccap ? cand[j] : ~0ull;
-            const bool f = cv <= T;
+        for (int base = 0; base < ccap; base += kThreads * kSamplePer) {
+            const int j0 = base + threadIdx.x * kSamplePer;
+            int nf = 0;
+#pragma unroll
+            for (int u = 0; u < kSamplePer; ++u) nf += (j0 + u < ccap && cand[j0 + u] <= T) ? 1 : 0;
             int tot;
-            const int off = block_exclusive_scan(f ? 1 : 0, scan_tmp, &tot);
-            if (f) a.extra[eoff + ne + off] = (uint32_t)(cv & 0xFFFFFFFFull);
+            int off = ne + block_exclusive_scan(nf, scan_tmp, &tot);
+#pragma unroll
+            for (int u = 0; u < kSamplePer; ++u) {
+                if (j0 + u < ccap) {
+                    const unsigned long long cv = cand[j0 + u];
+                    if (cv <= T) a.extra[eoff + off++] = (uint32_t)(cv & 0xFFFFFFFFull);
+                }
+            }
             ne += tot;
         }
         if (threadIdx.x == 0) a.extra_cnt[h] = ne;
@@ -546,13 +698,18 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
 // Heavy rows, step 3: Gram/data partials of each chunk's certain visits and of
 // each row's chosen candidates.
 template <int RP, int EW, bool BF16>
+struct HeavyGramSmem {
+    using G = Gram<RP, EW, BF16>;
+    __host__ __device__ static constexpr size_t bytes(int no) { return G::region_bytes(no) + (size_t)G::PW * 4; }
+};
+
+template <int RP, int EW, bool BF16>
 __global__ void __launch_bounds__(kThreads, 2) k_heavy_gram(ModeArgs a) {
     using G = Gram<RP, EW, BF16>;
-    extern __shared__ __align__(16) float smem[];
-    float* tile = smem;
-    float* red = smem;
-    constexpr int A = G::SM_TILE > G::SM_RED ? G::SM_TILE : G::SM_RED;
-    float* sum = smem + A;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* pipe = smem_raw;
+    float* red = reinterpret_cast<float*>(smem_raw);
+    float* sum = reinterpret_cast<float*>(smem_raw + G::region_bytes(a.n_other));
     const int item = blockIdx.x;
     const uint32_t* list;
     int cnt;
@@ -567,16 +724,45 @@ __global__ void __launch_bounds__(kThreads, 2) k_heavy_gram(ModeArgs a) {
     G gr;
     gr.init();
     auto getpos = [&](int v) -> uint32_t { return list[v]; };
-    gr.run(a, getpos, cnt, tile);
+    gr.run(a, getpos, cnt, pipe);
     gr.reduce(red, sum);
     float* out = a.partial + (size_t)item * G::PW;
     for (int s = threadIdx.x; s < G::PW; s += kThreads) out[s] = sum[s];
 }
 
-// Heavy rows, step 4: fixed-order sum of a row's partials, then the row update.
+// Heavy rows, step 4a: a row's items (its chunks in order, then its chosen
+// candidates) are summed in fixed groups of kReduceGroup consecutive items,
+// one block per group, so that long rows are not summed by a single block.
+constexpr int kReduceGroup = 16;
+
+template <int RP>
+__global__ void __launch_bounds__(kThreads) k_heavy_reduce(ModeArgs a) {
+    constexpr int T = RP / 8, NP = T * (T + 1) / 2, PW = NP * 64 + RP;
+    const int4 gr = a.groups[blockIdx.x];   // {heavy row, first item, end item, 0}
+    const int h = gr.x;
+    const int4 hv = a.heavy[h];
+    const int nitems = hv.w - hv.z + 1;
+    float* out = a.partial2 + (size_t)blockIdx.x * PW;
+    for (int s = threadIdx.x; s < PW; s += kThreads) {
+        float v[kReduceGroup];
+#pragma unroll
+        for (int u = 0; u < kReduceGroup; ++u) {
+            const int i = gr.y + u;
+            const int it = i < nitems - 1 ? hv.z + i : a.n_chunks + h;
+            v[u] = i < gr.z ? a.partial[(size_t)it * PW + s] : 0.f;
+        }
+        float t = 0.f;
+#pragma unroll
+        for (int u = 0; u < kReduceGroup; ++u) t += v[u];
+        out[s] = t;
+    }
+}
+
+// Heavy rows, step 4b: fixed-order sum of the row's group sums, then the row
+// update.
 template <int RP>
 __global__ void __launch_bounds__(kThreads) k_heavy_finish(ModeArgs a) {
-    constexpr int T = RP / 8, NP = T * (T + 1) / 2, PW = NP * 72;
+    constexpr int T = RP / 8, NP = T * (T + 1) / 2, PW = NP * 64 + RP;
     extern __shared__ __align__(16) float smem[];
     float* sum = smem;
     float* H = sum + PW;
@@ -584,10 +770,18 @@ __global__ void __launch_bounds__(kThreads) k_heavy_finish(ModeArgs a) {
     float* vsh = bvec + RP;
     const int h = blockIdx.x;
     const int4 hv = a.heavy[h];
+    const int2 gg = a.heavy_groups[h];   // {first group, end group}
     for (int s = threadIdx.x; s < PW; s += kThreads) {
         float t = 0.f;
-        for (int ch = hv.z; ch < hv.w; ++ch) t += a.partial[(size_t)ch * PW + s];
-        t += a.partial[(size_t)(a.n_chunks + h) * PW + s];
+        int g = gg.x;
+        for (; g + 8 <= gg.y; g += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = a.partial2[(size_t)(g + u) * PW + s];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t += v[u];
+        }
+        for (; g < gg.y; ++g) t += a.partial2[(size_t)g * PW + s];
         sum[s] = t;
     }
     __syncthreads();
@@ -613,13 +807,7 @@ __global__ void k_heavy_mask(ModeArgs a) {
 
 template <int RP>
 constexpr size_t heavy_finish_smem() {
-    return (size_t)((RP / 8) * (RP / 8 + 1) / 2 * 72 + RP * (RP + 1) + 2 * RP + 8) * 4;
-}
-
-template <int RP, int EW, bool BF16>
-constexpr size_t heavy_gram_smem() {
-    using G = Gram<RP, EW, BF16>;
-    return (size_t)((G::SM_TILE > G::SM_RED ? G::SM_TILE : G::SM_RED) + G::SM_SUM) * 4;
+    return (size_t)((RP / 8) * (RP / 8 + 1) / 2 * 64 + RP + RP * (RP + 1) + 2 * RP + 8) * 4;
 }
 
 }  // namespace ntc

@@ -58,7 +58,8 @@ struct ModePlan {
     int64_t visits = 0, visits_heavy = 0, rows_updated = 0, rows_skipped = 0;
     int n_light = 0, n_heavy = 0, n_chunks = 0;
     int64_t cand_total = 0, extra_total = 0;
-    DevMem light_rows, light_k, chunks, chunk_caps, heavy, bracket, heavy_cand;
+    int n_groups = 0;
+    DevMem light_rows, light_k, chunks, chunk_caps, heavy, bracket, heavy_cand, groups, heavy_groups;
 };
 
 int pad_rank(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
@@ -90,7 +91,7 @@ struct ntc_handle {
     std::vector<int64_t> row_ptr_h[kMaxOrder];
     ModePlan plan[kMaxOrder];
     // scratch
-    DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, stat, red, mask;
+    DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, partial2, stat, red, mask;
     // per-kernel event timing ("profile")
     int profile = 0;
     struct Pending {
@@ -173,8 +174,10 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
     static bool attr = false;
     if (!attr) {
         cudaError_t e;
-        if ((e = set_smem(k_light<RP, EW, BF>, LightSmem<RP, EW, BF>::BYTES)) != cudaSuccess) return e;
-        if ((e = set_smem(k_heavy_gram<RP, EW, BF>, heavy_gram_smem<RP, EW, BF>())) != cudaSuccess) return e;
+        constexpr int nomax = Gram<RP, EW, BF>::NOMAX;
+        if ((e = set_smem(k_light<RP, EW, BF>, LightSmem<RP, EW, BF>::bytes(nomax))) != cudaSuccess) return e;
+        if ((e = set_smem(k_heavy_gram<RP, EW, BF>, HeavyGramSmem<RP, EW, BF>::bytes(nomax))) != cudaSuccess)
+            return e;
         if ((e = set_smem(k_heavy_finish<RP>, heavy_finish_smem<RP>())) != cudaSuccess) return e;
         attr = true;
     }
@@ -182,28 +185,31 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
     if (p.n_light > 0) {
         const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv + (int64_t)p.n_light * L.bpr;
         e = L.run(NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
-            k_light<RP, EW, BF><<<p.n_light, kThreads, LightSmem<RP, EW, BF>::BYTES, s>>>(a);
+            k_light<RP, EW, BF><<<p.n_light, kThreads, LightSmem<RP, EW, BF>::bytes(a.n_other), s>>>(a);
         });
         if (e != cudaSuccess) return e;
     }
     if (p.n_heavy > 0) {
         e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
         if (e != cudaSuccess) return e;
-        e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_heavy_sample<<<p.n_chunks, kThreads, 0, s>>>(a); });
+        e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_heavy_sample<EW><<<p.n_chunks, kThreads, 0, s>>>(a); });
         if (e != cudaSuccess) return e;
-        e = L.run(NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<<<p.n_heavy, kThreads, 0, s>>>(a); });
+        e = L.run(NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<EW><<<p.n_heavy, kThreads, 0, s>>>(a); });
         if (e != cudaSuccess) return e;
         if (mask_only) {
             k_heavy_mask<<<p.n_chunks + p.n_heavy, kThreads, 0, s>>>(a);
             ++*L.launches;
         } else {
             e = L.run(NTC_K_HEAVY_GRAM, p.visits_heavy * L.bpv, [&] {
-                k_heavy_gram<RP, EW, BF><<<p.n_chunks + p.n_heavy, kThreads, heavy_gram_smem<RP, EW, BF>(), s>>>(a);
+                k_heavy_gram<RP, EW, BF><<<p.n_chunks + p.n_heavy, kThreads,
+                                           HeavyGramSmem<RP, EW, BF>::bytes(a.n_other), s>>>(a);
             });
             if (e != cudaSuccess) return e;
             e = L.run(NTC_K_HEAVY_FINISH, (int64_t)p.n_heavy * L.bpr, [&] {
+                k_heavy_reduce<RP><<<p.n_groups, kThreads, 0, s>>>(a);
                 k_heavy_finish<RP><<<p.n_heavy, kThreads, heavy_finish_smem<RP>(), s>>>(a);
             });
+            ++*L.launches;
             if (e != cudaSuccess) return e;
         }
     }
@@ -227,7 +233,7 @@ cudaError_t launch_mode(int rp, int ew, bool bf, const ModeArgs& a, const ModePl
 
 int partial_width(int rp) {
     const int T = rp / 8;
-    return T * (T + 1) / 2 * 72;
+    return T * (T + 1) / 2 * 64 + rp;
 }
 
 // ---- per-(mode, c) plan ------------------------------------------------------
@@ -241,7 +247,8 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     const int64_t P = h->dims[mode];
     std::vector<std::pair<int64_t, int32_t>> light;   // (n, row)
     std::vector<int32_t> light_k;
-    std::vector<int4> chunks, caps, heavy, hcand;
+    std::vector<int4> chunks, caps, heavy, hcand, groups;
+    std::vector<int2> heavy_groups;
     std::vector<longlong2> brk;
     int64_t visits = 0, visits_heavy = 0, updated = 0, skipped = 0, cand_total = 0, extra_total = 0;
     for (int64_t r = 0; r < P; ++r) {
@@ -287,6 +294,13 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
             cand_total += cap;
         }
         heavy.push_back(make_int4((int)r, (int)k, cb, (int)chunks.size()));
+        {
+            const int nitems = (int)chunks.size() - cb + 1;   // chunks, then the chosen candidates
+            const int g0 = (int)groups.size();
+            for (int i = 0; i < nitems; i += kReduceGroup)
+                groups.push_back(make_int4(hidx, i, std::min(nitems, i + kReduceGroup), 0));
+            heavy_groups.push_back(make_int2(g0, (int)groups.size()));
+        }
         brk.push_back(make_longlong2(lo, hi));
         const int ccap = (int)(cand_total - cbeg);
         hcand.push_back(make_int4((int)cbeg, ccap, (int)extra_total, ccap));
@@ -317,6 +331,8 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     NTC_CUDA(h, up(p.heavy, heavy.data(), heavy.size() * sizeof(int4)));
     NTC_CUDA(h, up(p.bracket, brk.data(), brk.size() * sizeof(longlong2)));
     NTC_CUDA(h, up(p.heavy_cand, hcand.data(), hcand.size() * sizeof(int4)));
+    NTC_CUDA(h, up(p.groups, groups.data(), groups.size() * sizeof(int4)));
+    NTC_CUDA(h, up(p.heavy_groups, heavy_groups.data(), heavy_groups.size() * sizeof(int2)));
     NTC_CUDA(h, cudaStreamSynchronize(h->stream));   // host vectors go out of scope
     p.c = c;
     p.heavy_threshold = h->heavy_threshold;
@@ -329,6 +345,7 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     p.n_light = (int)light.size();
     p.n_heavy = (int)heavy.size();
     p.n_chunks = (int)chunks.size();
+    p.n_groups = (int)groups.size();
     p.cand_total = cand_total;
     p.extra_total = extra_total;
     // scratch sized for this plan
@@ -341,6 +358,7 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     NTC_CUDA(h, h->flags.ensure(sizeof(uint32_t) * (size_t)std::max(p.n_heavy, 1)));
     NTC_CUDA(h, h->partial.ensure(sizeof(float) * (size_t)partial_width(h->rp) *
                                   (size_t)std::max(p.n_chunks + p.n_heavy, 1)));
+    NTC_CUDA(h, h->partial2.ensure(sizeof(float) * (size_t)partial_width(h->rp) * (size_t)std::max(p.n_groups, 1)));
     p.valid = true;
     return NTC_OK;
 }
@@ -389,6 +407,10 @@ ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t a
     a.extra_cnt = h->extra_cnt.as<uint32_t>();
     a.flags = h->flags.as<uint32_t>();
     a.partial = h->partial.as<float>();
+    a.groups = p.groups.as<int4>();
+    a.heavy_groups = p.heavy_groups.as<int2>();
+    a.n_groups = p.n_groups;
+    a.partial2 = h->partial2.as<float>();
     a.stat_fallback = h->stat.as<unsigned long long>();
     a.mask_out = nullptr;
     return a;

@@ -26,12 +26,12 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
                                                  uint32_t c3, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        c0 = hi1 ^ c1 ^ k0;
-        c1 = lo1;
-        c2 = hi0 ^ c3 ^ k1;
-        c3 = lo0;
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        c1 = (uint32_t)p1;
+        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c3 = (uint32_t)p0;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -147,6 +147,10 @@ struct ModeArgs {
     uint32_t* extra_cnt;      // [n_heavy]
     uint32_t* flags;          // [n_heavy]: 1 = candidate overflow
     float* partial;           // [(n_chunks + n_heavy)][pw]
+    const int4* groups;       // reduction groups {heavy row, first item, end item, 0}
+    const int2* heavy_groups; // per heavy row {first group, end group}
+    int n_groups;
+    float* partial2;          // [n_groups][pw]
     unsigned long long* stat_fallback;  // counter of rows that used the exact selector
     uint8_t* mask_out;        // sampler-only mode: mask over bucket positions
 };
