@@ -77,6 +77,11 @@ struct ntc_handle {
     double bracket_z = 7.0;
     int heavy_threshold = 4096, chunk = 16384;
     cudaStream_t stream = nullptr;
+    // light rows run on a side stream beside the split-row kernels of the same
+    // mode update (they write disjoint rows); fork/join through two events
+    int overlap = 1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     // state
     uint64_t ao_iter = 0;
@@ -107,6 +112,9 @@ struct ntc_handle {
             cudaEventDestroy(q.a);
             cudaEventDestroy(q.b);
         }
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
     }
 };
 
@@ -149,7 +157,9 @@ struct Launcher {
     int64_t* launches;
     int64_t bpv, bpr;   // algorithmic bytes per visit and per row update
     template <class F>
-    cudaError_t run(int kind, int64_t bytes, F&& f) {
+    cudaError_t run(int kind, int64_t bytes, F&& f) { return run_on(s, kind, bytes, f); }
+    template <class F>
+    cudaError_t run_on(cudaStream_t s, int kind, int64_t bytes, F&& f) {
         cudaEvent_t a = nullptr, b = nullptr;
         if (h->profile) {
             cudaError_t e = cudaEventCreate(&a);
@@ -182,12 +192,25 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         attr = true;
     }
     cudaError_t e = cudaSuccess;
+    const bool fork = p.n_light > 0 && p.n_heavy > 0 && L.h->overlap;
+    if (fork) {
+        ntc_handle* h = L.h;
+        if (!h->side) {
+            if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+    }
     if (p.n_light > 0) {
         const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv + (int64_t)p.n_light * L.bpr;
-        e = L.run(NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
-            k_light<RP, EW, BF><<<p.n_light, kThreads, LightSmem<RP, EW, BF>::bytes(a.n_other), s>>>(a);
+        cudaStream_t ls = fork ? L.h->side : s;
+        e = L.run_on(ls, NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
+            k_light<RP, EW, BF><<<p.n_light, kThreads, LightSmem<RP, EW, BF>::bytes(a.n_other), ls>>>(a);
         });
         if (e != cudaSuccess) return e;
+        if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;
     }
     if (p.n_heavy > 0) {
         e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
@@ -213,6 +236,7 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
             if (e != cudaSuccess) return e;
         }
     }
+    if (fork && (e = cudaStreamWaitEvent(s, L.h->ev_join, 0)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -682,6 +706,8 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
     } else if (k == "init_seed") {
         if (!(v >= 0)) return fail(h, NTC_ERR_ARG, "init_seed must be >= 0");
         h->init_seed = (uint64_t)v;
+    } else if (k == "overlap") {
+        h->overlap = v != 0.0;
     } else if (k == "profile") {
         h->profile = v != 0.0;
     } else if (k == "keep_perm") {
