@@ -10,8 +10,8 @@ namespace ntc {
 
 // ---------------------------------------------------------------------------
 // Block radix select.  Items are unique 64-bit composites (key << 32 | bucket
-// position).  Returns T such that exactly k items satisfy composite <= T
-// (1 <= k <= n): the k-th smallest composite, or, when a whole radix bucket
+// position), or ~0 for an unused slot.  Returns T such that exactly k items
+// satisfy composite <= T (1 <= k <= number of items): the k-th smallest composite, or, when a whole radix bucket
 // completes the count early, the largest composite that bucket can hold.
 // This is how "the k_p positions with the smallest (key, position)" of the
 // sampling rule (Sec. II-B, Alg. 1 line 5) are found without a sort.
@@ -27,6 +27,9 @@ __device__ unsigned long long block_select_kth(const Get& get, int n, int k, uns
         __syncthreads();
         for (int j = tid; j < n; j += kThreads) {
             const unsigned long long c = get(j);
+            // ~0 marks an unused slot; it is larger than every item, so
+            // leaving it out cannot change the k-th smallest (k <= items)
+            if (c == ~0ull) continue;
             const bool match = pass == 0 || ((c ^ prefix) >> (shift + 8)) == 0ull;
             if (match) atomicAdd(&hist[(c >> shift) & 255u], 1u);
         }
@@ -107,11 +110,11 @@ __device__ __forceinline__ void cp_async_wait() {
 // the FMA pass of tile t and the product pass of tile t+1 while the factor
 // rows of tiles t+2, t+3 and the entries of tiles t+4, t+5 are in flight and
 // the bucket positions of tile t+6 are loaded into registers.
-template <int RP, int EW, bool BF16>
+template <int RP, int EW, bool BF16, int NT = kThreads>
 struct Gram {
     static constexpr int T = RP / 8;
     static constexpr int NP = T * (T + 1) / 2;
-    static constexpr int NG = kThreads / NP;
+    static constexpr int NG = NT / NP;
     static constexpr int NACT = NG * NP;
     static constexpr int ES = BF16 ? 2 : 4;           // bytes per stored factor element
     static constexpr int ROWB = RP * ES;              // bytes per factor row
@@ -126,15 +129,15 @@ struct Gram {
     static constexpr int NOTYP = EW == 4 ? 2 : 4;     // other modes the tile size is tuned for
     static constexpr int BPV_TYP = SR * NOTYP * RST + SE * ENTB + 2 * KST * 4;
     static constexpr int BPV_MAX = SR * NOMAX * RST + SE * ENTB + 2 * KST * 4;
-    static constexpr int VT_BUDGET = 100000 / BPV_TYP;
+    static constexpr int VT_BUDGET = (NT >= 256 ? 100000 : 50000) / BPV_TYP;
     static constexpr int VT_MAX = 200000 / BPV_MAX;
     static constexpr int VT0 = VT_BUDGET < VT_MAX ? VT_BUDGET : VT_MAX;
     static constexpr int VT1 = VT0 >= NG ? (VT0 / NG) * NG : VT0;
-    static constexpr int VT = VT1 > 256 ? 256 : (VT1 < 1 ? 1 : VT1);   // visits per staged tile
+    static constexpr int VT = VT1 > NT ? NT : (VT1 < 1 ? 1 : VT1);     // visits per staged tile
     static constexpr int VPG = (VT + NG - 1) / NG;    // visits per group per tile
     static constexpr int PW = NP * 64 + RP;           // reduced floats: the tiles, then b
-    static constexpr int RED_BYTES = (NACT * 64 + kThreads * 4) * 4;
-    static_assert(kThreads % QPV == 0, "a thread's product-pass quad must be fixed");
+    static constexpr int RED_BYTES = (NACT * 64 + NT * 4) * 4;
+    static_assert(NT % QPV == 0, "a thread's product-pass quad must be fixed");
 
     __host__ __device__ static constexpr size_t pipe_bytes(int no) {
         return (size_t)SR * no * VT * RST + (size_t)SE * VT * ENTB + (size_t)2 * VT * KST * 4;
@@ -179,7 +182,7 @@ struct Gram {
     __device__ __forceinline__ void product(const unsigned char* rows, const Entry<EW>* ents, float* kt, int nv,
                                             int no) {
         const int q = threadIdx.x % QPV;
-        for (int s = threadIdx.x; s < nv * QPV; s += kThreads) {
+        for (int s = threadIdx.x; s < nv * QPV; s += NT) {
             const int v = s / QPV;
             float4 p = load4(rows + (size_t)v * RST, q);
             for (int o = 1; o < no; ++o) {
@@ -249,7 +252,7 @@ struct Gram {
             unsigned char* r = rows + (size_t)(t % SR) * stage_rows;
             // copy i = (o * VT + v) * CPR + c; VT and CPR are compile-time constants
             const int total = no * VT * CPR;
-            for (int i = tid; i < total; i += kThreads) {
+            for (int i = tid; i < total; i += NT) {
                 const int c = i % CPR;
                 const int vo = i / CPR;
                 const int v = vo % VT;
@@ -313,17 +316,17 @@ struct Gram {
         }
         reinterpret_cast<float4*>(red + NACT * 64)[threadIdx.x] = bq;
         __syncthreads();
-        for (int s = threadIdx.x; s < NP * 64; s += kThreads) {
+        for (int s = threadIdx.x; s < NP * 64; s += NT) {
             const int p = s >> 6, ij = s & 63;
             const float* col = red + ij * NACT + p;
             float t = 0.f;
             for (int gg = 0; gg < NG; ++gg) t += col[gg * NP];
             sum[s] = t;
         }
-        for (int r = threadIdx.x; r < RP; r += kThreads) {
+        for (int r = threadIdx.x; r < RP; r += NT) {
             const int q = r / 4, c = r % 4;
             float t = 0.f;
-            for (int th = q; th < kThreads; th += QPV) t += red[NACT * 64 + th * 4 + c];
+            for (int th = q; th < NT; th += QPV) t += red[NACT * 64 + th * 4 + c];
             sum[NP * 64 + r] = t;
         }
         __syncthreads();
@@ -548,10 +551,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
 // consecutive positions per round, so one block scan serves 2048 positions.
 constexpr int kSamplePer = 8;
 
-template <int EW>
-__global__ void __launch_bounds__(kThreads) k_heavy_sample(ModeArgs a) {
-    __shared__ int scan_tmp[kThreads / 32 + 1];
-    const int ch = blockIdx.x;
+// Keys of chunk `ch`: certain positions to a.vis[pb ...] in position order,
+// candidates to the chunk's candidate slots; returns the certain count (the
+// same in every thread).
+__device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan_tmp) {
     const int4 c = a.chunks[ch];
     const int h = c.x;
     const uint32_t pb = (uint32_t)c.y, pe = (uint32_t)c.z;
@@ -598,6 +601,13 @@ __global__ void __launch_bounds__(kThreads) k_heavy_sample(ModeArgs a) {
         a.cand_cnt[ch] = min(ncand, cap);
         if (ncand > cap) atomicOr(&a.flags[h], 1u);
     }
+    return nsel;
+}
+
+template <int EW>
+__global__ void __launch_bounds__(kThreads) k_heavy_sample(ModeArgs a) {
+    __shared__ int scan_tmp[kThreads / 32 + 1];
+    sample_chunk(a, blockIdx.x, scan_tmp);
 }
 
 // Heavy rows, step 2: per row, the certain count C plus the m = k - C
@@ -697,15 +707,17 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
 
 // Heavy rows, step 3: Gram/data partials of each chunk's certain visits and of
 // each row's chosen candidates.
+constexpr int kGramThreads = 256;   // threads per block of the split-row Gram
+
 template <int RP, int EW, bool BF16>
 struct HeavyGramSmem {
-    using G = Gram<RP, EW, BF16>;
+    using G = Gram<RP, EW, BF16, kGramThreads>;
     __host__ __device__ static constexpr size_t bytes(int no) { return G::region_bytes(no) + (size_t)G::PW * 4; }
 };
 
 template <int RP, int EW, bool BF16>
-__global__ void __launch_bounds__(kThreads, 2) k_heavy_gram(ModeArgs a) {
-    using G = Gram<RP, EW, BF16>;
+__global__ void __launch_bounds__(kGramThreads, 2) k_heavy_gram(ModeArgs a) {
+    using G = Gram<RP, EW, BF16, kGramThreads>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* pipe = smem_raw;
     float* red = reinterpret_cast<float*>(smem_raw);
@@ -727,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_heavy_gram(ModeArgs a) {
     gr.run(a, getpos, cnt, pipe);
     gr.reduce(red, sum);
     float* out = a.partial + (size_t)item * G::PW;
-    for (int s = threadIdx.x; s < G::PW; s += kThreads) out[s] = sum[s];
+    for (int s = threadIdx.x; s < G::PW; s += kGramThreads) out[s] = sum[s];
 }
 
 // Heavy rows, step 4a: a row's items (its chunks in order, then its chosen
