@@ -166,10 +166,21 @@ __global__ void k_row_ptr(const uint32_t* keys, int64_t n, int64_t dim, int64_t*
     }
 }
 
-// Bucket entries of `mode` in sorted order: other modes' indices, then value.
+// Observations per row of `mode` (exact integer histogram).
+__global__ void k_count_rows(const int32_t* idx, int64_t n, int order, int mode, uint32_t* counts) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&counts[idx[e * order + mode]], 1u);
+}
+
+struct RowMaps {
+    const int32_t* inv[kMaxOrder];   // original row -> storage row, per mode
+};
+
+// Bucket entries of `mode` in sorted order: the other modes' indices mapped
+// to their storage rows, then the value.
 template <int EW>
 __global__ void k_fill_bucket(const int32_t* idx, const float* vals, const uint32_t* perm, int64_t n,
-                              int order, int mode, Entry<EW>* out) {
+                              int order, int mode, RowMaps maps, Entry<EW>* out) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = perm[q];
@@ -178,7 +189,7 @@ __global__ void k_fill_bucket(const int32_t* idx, const float* vals, const uint3
         for (int w = 0; w < EW; ++w) en.w[w] = 0;
         int o = 0;
         for (int i = 0; i < order; ++i)
-            if (i != mode) en.w[o++] = idx[e * order + i];
+            if (i != mode) en.w[o++] = maps.inv[i][idx[e * order + i]];
         en.w[EW - 1] = __float_as_int(vals[e]);
         out[q] = en;
     }
@@ -216,10 +227,12 @@ __global__ void __launch_bounds__(kThreads) k_sum_partials(const double* partial
 }
 
 // Initial factors: i.i.d. U[0, 2a] from Philox(counter {0xFFFF, mode, row,
-// col}, key init_seed), u = (word0 + 1/2) 2^-32, drawn in double, stored
-// rounded to float; padding columns are zero.
+// col}, key init_seed) with `row` the original row index, u = (word0 + 1/2)
+// 2^-32, drawn in double, stored rounded to float at the row's storage slot;
+// padding columns are zero.
 __global__ void k_init_factor(float* U, uint16_t* Ub, int64_t rows, int R, int rp, int mode,
-                              const double* sum_vals, int64_t nnz, int order, uint32_t k0, uint32_t k1) {
+                              const double* sum_vals, int64_t nnz, int order, uint32_t k0, uint32_t k1,
+                              const int32_t* perm_rows) {
     const double mean = nnz > 0 ? *sum_vals / (double)nnz : 0.0;
     const double a = mean > 0.0 ? pow(mean / (double)R, 1.0 / (double)order) : 0.0;
     const int64_t total = rows * rp;
@@ -229,7 +242,8 @@ __global__ void k_init_factor(float* U, uint16_t* Ub, int64_t rows, int R, int r
         const int r = (int)(t - p * rp);
         float v = 0.f;
         if (r < R) {
-            const uint4 w = philox4(0xFFFFu, (uint32_t)mode, (uint32_t)p, (uint32_t)r, k0, k1);
+            const uint32_t orig = (uint32_t)perm_rows[p];
+            const uint4 w = philox4(0xFFFFu, (uint32_t)mode, orig, (uint32_t)r, k0, k1);
             const double u = ((double)w.x + 0.5) * (1.0 / 4294967296.0);
             v = (float)(2.0 * a * u);
         }
@@ -245,15 +259,18 @@ __global__ void k_to_bf16(const float* U, uint16_t* Ub, int64_t n) {
 
 struct FactorSet {
     const float* U[kMaxOrder];
+    const int32_t* inv[kMaxOrder];   // original row -> storage row
     int order, R, rp;
 };
 
 // Model value (eq. 1) at one index, float32 products and sum.
 __device__ __forceinline__ float model_at(const FactorSet& f, const int32_t* ix) {
+    const float* row[kMaxOrder];
+    for (int i = 0; i < f.order; ++i) row[i] = f.U[i] + (size_t)f.inv[i][ix[i]] * f.rp;
     float acc = 0.f;
     for (int r = 0; r < f.R; ++r) {
-        float p = f.U[0][(size_t)ix[0] * f.rp + r];
-        for (int i = 1; i < f.order; ++i) p *= f.U[i][(size_t)ix[i] * f.rp + r];
+        float p = row[0][r];
+        for (int i = 1; i < f.order; ++i) p *= row[i][r];
         acc += p;
     }
     return acc;

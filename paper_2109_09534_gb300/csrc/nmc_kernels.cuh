@@ -110,7 +110,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // the FMA pass of tile t and the product pass of tile t+1 while the factor
 // rows of tiles t+2, t+3 and the entries of tiles t+4, t+5 are in flight and
 // the bucket positions of tile t+6 are loaded into registers.
-template <int RP, int EW, bool BF16, int NT = kThreads>
+template <int RP, int EW, bool BF16, int NT = kThreads, int NHOT = 0>
 struct Gram {
     static constexpr int T = RP / 8;
     static constexpr int NP = T * (T + 1) / 2;
@@ -142,9 +142,12 @@ struct Gram {
     __host__ __device__ static constexpr size_t pipe_bytes(int no) {
         return (size_t)SR * no * VT * RST + (size_t)SE * VT * ENTB + (size_t)2 * VT * KST * 4;
     }
+    // the most frequent NHOT rows of each other mode, resident for the block
+    __host__ __device__ static constexpr size_t hot_bytes(int no) { return (size_t)no * NHOT * RST; }
     __host__ __device__ static constexpr size_t region_bytes(int no) {
         return pipe_bytes(no) > (size_t)RED_BYTES ? pipe_bytes(no) : (size_t)RED_BYTES;
     }
+    __host__ __device__ static constexpr size_t total_bytes(int no) { return region_bytes(no) + hot_bytes(no); }
 
     float acc[8][8];
     float4 bq;       // b partial of this thread's product-pass quad
@@ -178,15 +181,21 @@ struct Gram {
         return *reinterpret_cast<const float4*>(row + q * 16);
     }
 
-    // k rows of tile visits [0, nv) into the k-tile; b += x k.
+    // k rows of tile visits [0, nv) into the k-tile; b += x k.  Rows of the
+    // hot set are read from the resident copy.
     __device__ __forceinline__ void product(const unsigned char* rows, const Entry<EW>* ents, float* kt, int nv,
-                                            int no) {
+                                            int no, const unsigned char* hot, int nhot) {
         const int q = threadIdx.x % QPV;
         for (int s = threadIdx.x; s < nv * QPV; s += NT) {
             const int v = s / QPV;
-            float4 p = load4(rows + (size_t)v * RST, q);
+            auto row_of = [&](int o) -> const unsigned char* {
+                const int idx = ents[v].w[o];
+                return (NHOT > 0 && idx < nhot) ? hot + ((size_t)o * NHOT + idx) * RST
+                                                : rows + ((size_t)o * VT + v) * RST;
+            };
+            float4 p = load4(row_of(0), q);
             for (int o = 1; o < no; ++o) {
-                const float4 u = load4(rows + ((size_t)o * VT + v) * RST, q);
+                const float4 u = load4(row_of(o), q);
                 p.x *= u.x;
                 p.y *= u.y;
                 p.z *= u.z;
@@ -227,6 +236,15 @@ struct Gram {
     __device__ __forceinline__ void run(const ModeArgs& a, const GetPos& getpos, int nvis, unsigned char* pipe) {
         const int no = a.n_other;
         const int tid = threadIdx.x;
+        unsigned char* hot = pipe + region_bytes(no);                                   // [no][NHOT][RST]
+        const int nhot = NHOT > 0 ? min(NHOT, a.nhot) : 0;
+        if (NHOT > 0) {
+            for (int i = tid; i < no * nhot * CPR; i += NT) {
+                const int c = i % CPR, ro = i / CPR, r = ro % nhot, o = ro / nhot;
+                cp_async16_ca(hot + ((size_t)o * NHOT + r) * RST + 16 * c,
+                              static_cast<const unsigned char*>(a.other[o]) + (size_t)r * ROWB + 16 * c);
+            }
+        }
         const size_t stage_rows = (size_t)no * VT * RST;
         unsigned char* rows = pipe;                                                       // [SR][no][VT][RST]
         Entry<EW>* ents = reinterpret_cast<Entry<EW>*>(pipe + SR * stage_rows);          // [SE][VT]
@@ -258,15 +276,16 @@ struct Gram {
                 const int v = vo % VT;
                 const int o = vo / VT;
                 if (v >= nv) continue;
-                const unsigned char* src = static_cast<const unsigned char*>(a.other[o]) +
-                                           (size_t)e[v].w[o] * ROWB + 16 * c;
+                const int idx = e[v].w[o];
+                if (NHOT > 0 && idx < nhot) continue;   // resident
+                const unsigned char* src = static_cast<const unsigned char*>(a.other[o]) + (size_t)idx * ROWB + 16 * c;
                 cp_async16_ca(r + (size_t)vo * RST + 16 * c, src);
             }
         };
         auto do_product = [&](int t) {
             if (t < ntiles)
                 product(rows + (size_t)(t % SR) * stage_rows, ents + (t % SE) * VT, ktile + (t & 1) * VT * KST,
-                        tile_n(t), no);
+                        tile_n(t), no, hot, nhot);
         };
         // prologue: k-tile 0 formed; rows 1, 2 and entries 3, 4 in flight;
         // the position of tile 5 in a register
@@ -385,7 +404,7 @@ __device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float
     constexpr int PER = RP > 32 ? RP / 32 : 1;
     const int lane = threadIdx.x;
     const int R = a.rank;
-    const size_t base = (size_t)p * RP;
+    const size_t base = (size_t)a.inv_self[p] * RP;
     float y[PER], al[PER], grad[PER], v[PER], w[PER];
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
@@ -708,20 +727,28 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
 // Heavy rows, step 3: Gram/data partials of each chunk's certain visits and of
 // each row's chosen candidates.
 constexpr int kGramThreads = 256;   // threads per block of the split-row Gram
+// Resident most-frequent rows per other mode in the split-row Gram.  Off:
+// measured on the Zipf(1.1) 10^4-cube, R = 32, the copies it saves cost less
+// than the per-visit selection it adds (28.4 vs 32.5 ms/epoch); the L1-cached
+// row copies already serve the hot rows.
+template <int RP>
+struct HotRows {
+    static constexpr int value = 0;
+};
 
 template <int RP, int EW, bool BF16>
 struct HeavyGramSmem {
-    using G = Gram<RP, EW, BF16, kGramThreads>;
-    __host__ __device__ static constexpr size_t bytes(int no) { return G::region_bytes(no) + (size_t)G::PW * 4; }
+    using G = Gram<RP, EW, BF16, kGramThreads, HotRows<RP>::value>;
+    __host__ __device__ static constexpr size_t bytes(int no) { return G::total_bytes(no) + (size_t)G::PW * 4; }
 };
 
 template <int RP, int EW, bool BF16>
 __global__ void __launch_bounds__(kGramThreads, 2) k_heavy_gram(ModeArgs a) {
-    using G = Gram<RP, EW, BF16, kGramThreads>;
+    using G = Gram<RP, EW, BF16, kGramThreads, HotRows<RP>::value>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* pipe = smem_raw;
     float* red = reinterpret_cast<float*>(smem_raw);
-    float* sum = reinterpret_cast<float*>(smem_raw + G::region_bytes(a.n_other));
+    float* sum = reinterpret_cast<float*>(smem_raw + G::total_bytes(a.n_other));
     const int item = blockIdx.x;
     const uint32_t* list;
     int cnt;

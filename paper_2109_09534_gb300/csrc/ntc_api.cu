@@ -92,6 +92,12 @@ struct ntc_handle {
     // device data
     DevMem U[kMaxOrder], Ub[kMaxOrder], Y;
     DevMem row_ptr[kMaxOrder], bucket[kMaxOrder], perm[kMaxOrder];
+    // Factor rows are stored in descending order of their mode's observation
+    // counts (storage row = inv[original row], original row = rows[storage row]),
+    // so that the most frequent rows of a mode are its first storage rows.
+    // Identity until observations are set.  Bucket positions keep original order.
+    DevMem inv_dev[kMaxOrder], rows_dev[kMaxOrder];
+    std::vector<int32_t> inv_h[kMaxOrder], rows_h[kMaxOrder];
     DevMem coo_idx, coo_val, dims_dev;
     std::vector<int64_t> row_ptr_h[kMaxOrder];
     ModePlan plan[kMaxOrder];
@@ -397,12 +403,17 @@ ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t a
         a.other[o++] = h->storage_bf16 ? (const void*)h->Ub[i].p : (const void*)h->U[i].p;
     }
     a.n_other = h->order - 1;
+    int64_t nh = 64;   // the kernels cap this at their own resident-row count
+    for (int i = 0; i < h->order; ++i)
+        if (i != mode) nh = std::min<int64_t>(nh, h->dims[i]);
+    a.nhot = (int)nh;
     a.rank = h->rank;
     a.rp = h->rp;
     a.lambda = (float)h->lambda;
     a.lambda_d = h->lambda;
     a.power_iters = h->power_iters;
     a.U = h->U[mode].as<float>();
+    a.inv_self = h->inv_dev[mode].as<int32_t>();
     a.Ub = h->storage_bf16 ? h->Ub[mode].as<uint16_t>() : nullptr;
     a.Y = h->max_inner > 1 ? h->Y.as<float>() : nullptr;
     a.read_y = inner > 0 ? 1 : 0;
@@ -517,6 +528,49 @@ ntc_status sort_mode(ntc_handle* h, int mode, DevMem& k0, DevMem& k1, DevMem& v0
     return NTC_OK;
 }
 
+// Factor `mode` in original row order, [dims][rank] float32 (host).
+ntc_status download_factor(ntc_handle* h, int mode, float* out) {
+    const int64_t I = h->dims[mode];
+    const int R = h->rank, RP = h->rp;
+    std::vector<float> tmp((size_t)I * RP);
+    NTC_CUDA(h, cudaMemcpyAsync(tmp.data(), h->U[mode].p, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost,
+                                h->stream));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    const std::vector<int32_t>& inv = h->inv_h[mode];
+    for (int64_t r = 0; r < I; ++r) memcpy(out + r * R, tmp.data() + (size_t)inv[(size_t)r] * RP, sizeof(float) * R);
+    return NTC_OK;
+}
+
+// Store `in` ([dims][rank], original row order, host) as factor `mode`.
+ntc_status upload_factor(ntc_handle* h, int mode, const float* in) {
+    const int64_t I = h->dims[mode];
+    const int R = h->rank, RP = h->rp;
+    std::vector<float> tmp((size_t)I * RP, 0.f);
+    const std::vector<int32_t>& inv = h->inv_h[mode];
+    for (int64_t r = 0; r < I; ++r) memcpy(tmp.data() + (size_t)inv[(size_t)r] * RP, in + r * R, sizeof(float) * R);
+    NTC_CUDA(h, cudaMemcpyAsync(h->U[mode].p, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+    if (h->storage_bf16) {
+        const int64_t m = I * RP;
+        k_to_bf16<<<grid_for(m), 256, 0, h->stream>>>(h->U[mode].as<float>(), h->Ub[mode].as<uint16_t>(), m);
+        NTC_CUDA(h, cudaGetLastError());
+    }
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return NTC_OK;
+}
+
+ntc_status upload_maps(ntc_handle* h, int mode) {
+    const size_t I = (size_t)h->dims[mode];
+    NTC_CUDA(h, h->inv_dev[mode].ensure(sizeof(int32_t) * I));
+    NTC_CUDA(h, h->rows_dev[mode].ensure(sizeof(int32_t) * I));
+    NTC_CUDA(h, cudaMemcpyAsync(h->inv_dev[mode].p, h->inv_h[mode].data(), sizeof(int32_t) * I,
+                                cudaMemcpyHostToDevice, h->stream));
+    NTC_CUDA(h, cudaMemcpyAsync(h->rows_dev[mode].p, h->rows_h[mode].data(), sizeof(int32_t) * I,
+                                cudaMemcpyHostToDevice, h->stream));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return NTC_OK;
+}
+
 ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, const float* vals, bool dev) {
     if (!h) return NTC_ERR_ARG;
     if (nnz < 0 || nnz >= (1ll << 31) || (nnz > 0 && (!idx || !vals)))
@@ -549,6 +603,36 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
     h->nnz = nnz;
     h->ao_iter = 0;
     for (int i = 0; i < N; ++i) h->plan[i].valid = false;
+    // factors set by the caller keep their values across the renumbering
+    std::vector<std::vector<float>> kept(N);
+    for (int i = 0; i < N; ++i) {
+        if (!h->factor_set[i]) continue;
+        kept[i].resize((size_t)h->dims[i] * h->rank);
+        ntc_status st = download_factor(h, i, kept[i].data());
+        if (st != NTC_OK) return st;
+    }
+    // observation counts per row -> storage order (most frequent first, ties by row)
+    for (int i = 0; i < N; ++i) {
+        const int64_t I = h->dims[i];
+        DevMem cnt;
+        NTC_CUDA(h, cnt.ensure(sizeof(uint32_t) * (size_t)I));
+        NTC_CUDA(h, cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t) * (size_t)I, s));
+        if (nnz > 0) k_count_rows<<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), nnz, N, i, cnt.as<uint32_t>());
+        NTC_CUDA(h, cudaGetLastError());
+        std::vector<uint32_t> c((size_t)I);
+        NTC_CUDA(h, cudaMemcpyAsync(c.data(), cnt.p, sizeof(uint32_t) * (size_t)I, cudaMemcpyDeviceToHost, s));
+        NTC_CUDA(h, cudaStreamSynchronize(s));
+        std::vector<int32_t>& rows = h->rows_h[i];
+        rows.resize((size_t)I);
+        for (int64_t r = 0; r < I; ++r) rows[(size_t)r] = (int32_t)r;
+        std::stable_sort(rows.begin(), rows.end(), [&](int32_t x, int32_t y) { return c[(size_t)x] > c[(size_t)y]; });
+        h->inv_h[i].resize((size_t)I);
+        for (int64_t j = 0; j < I; ++j) h->inv_h[i][(size_t)rows[(size_t)j]] = (int32_t)j;
+        ntc_status st = upload_maps(h, i);
+        if (st != NTC_OK) return st;
+    }
+    RowMaps maps;
+    for (int i = 0; i < N; ++i) maps.inv[i] = h->inv_dev[i].as<int32_t>();
     // per-mode buckets
     DevMem k0, k1, v0, v1, hist, sums;
     const size_t nb4 = sizeof(uint32_t) * (size_t)std::max<int64_t>(nnz, 1);
@@ -570,10 +654,10 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
         if (nnz > 0) {
             if (EW == 4)
                 k_fill_bucket<4><<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), perm,
-                                                               nnz, N, i, h->bucket[i].as<Entry<4>>());
+                                                               nnz, N, i, maps, h->bucket[i].as<Entry<4>>());
             else
                 k_fill_bucket<8><<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), perm,
-                                                               nnz, N, i, h->bucket[i].as<Entry<8>>());
+                                                               nnz, N, i, maps, h->bucket[i].as<Entry<8>>());
         }
         if (h->keep_perm) {
             NTC_CUDA(h, h->perm[i].ensure(nb4));
@@ -594,10 +678,15 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
     k_sum_f32<<<gb, kThreads, 0, s>>>(h->coo_val.as<float>(), nnz, part.as<double>());
     k_sum_partials<<<1, kThreads, 0, s>>>(part.as<double>(), gb, tot.as<double>());
     for (int i = 0; i < N; ++i) {
-        if (h->factor_set[i]) continue;
+        if (h->factor_set[i]) {
+            ntc_status st = upload_factor(h, i, kept[i].data());
+            if (st != NTC_OK) return st;
+            continue;
+        }
         k_init_factor<<<grid_for(h->dims[i] * h->rp), 256, 0, s>>>(
             h->U[i].as<float>(), h->storage_bf16 ? h->Ub[i].as<uint16_t>() : nullptr, h->dims[i], h->rank, h->rp, i,
-            tot.as<double>(), nnz, N, (uint32_t)h->init_seed, (uint32_t)(h->init_seed >> 32));
+            tot.as<double>(), nnz, N, (uint32_t)h->init_seed, (uint32_t)(h->init_seed >> 32),
+            h->rows_dev[i].as<int32_t>());
     }
     NTC_CUDA(h, cudaGetLastError());
     NTC_CUDA(h, cudaStreamSynchronize(s));   // temporaries are freed on return
@@ -606,7 +695,10 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
 
 FactorSet factor_set(ntc_handle* h) {
     FactorSet f;
-    for (int i = 0; i < h->order; ++i) f.U[i] = h->U[i].as<float>();
+    for (int i = 0; i < h->order; ++i) {
+        f.U[i] = h->U[i].as<float>();
+        f.inv[i] = h->inv_dev[i].as<int32_t>();
+    }
     f.order = h->order;
     f.R = h->rank;
     f.rp = h->rp;
@@ -665,6 +757,17 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
         const size_t bytes = sizeof(float) * (size_t)dims[i] * h->rp;
         e = h->U[i].ensure(bytes);
         if (e == cudaSuccess) e = cudaMemset(h->U[i].p, 0, bytes);
+    }
+    for (int i = 0; i < order && e == cudaSuccess; ++i) {
+        h->inv_h[i].resize((size_t)dims[i]);
+        h->rows_h[i].resize((size_t)dims[i]);
+        for (int64_t r = 0; r < dims[i]; ++r) h->inv_h[i][(size_t)r] = h->rows_h[i][(size_t)r] = (int32_t)r;
+        e = h->inv_dev[i].ensure(sizeof(int32_t) * (size_t)dims[i]);
+        if (e == cudaSuccess) e = h->rows_dev[i].ensure(sizeof(int32_t) * (size_t)dims[i]);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->inv_dev[i].p, h->inv_h[i].data(), sizeof(int32_t) * dims[i], cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->rows_dev[i].p, h->rows_h[i].data(), sizeof(int32_t) * dims[i], cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = h->dims_dev.ensure(sizeof(int64_t) * kMaxOrder);
     if (e == cudaSuccess) e = cudaMemcpy(h->dims_dev.p, h->dims, sizeof(int64_t) * kMaxOrder, cudaMemcpyHostToDevice);
@@ -871,10 +974,7 @@ ntc_status ntc_cost(ntc_handle* h, double* out) {
 ntc_status ntc_get_factor(ntc_handle* h, int mode, float* out) {
     if (!h || !out || mode < 0 || mode >= h->order) return NTC_ERR_ARG;
     h->err.clear();
-    NTC_CUDA(h, cudaMemcpy2DAsync(out, sizeof(float) * h->rank, h->U[mode].p, sizeof(float) * h->rp,
-                                  sizeof(float) * h->rank, (size_t)h->dims[mode], cudaMemcpyDeviceToHost, h->stream));
-    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
-    return NTC_OK;
+    return download_factor(h, mode, out);
 }
 
 ntc_status ntc_set_factor(ntc_handle* h, int mode, const float* in) {
@@ -883,15 +983,8 @@ ntc_status ntc_set_factor(ntc_handle* h, int mode, const float* in) {
     const int64_t n = h->dims[mode] * (int64_t)h->rank;
     for (int64_t j = 0; j < n; ++j)
         if (!(in[j] >= 0.0f) || std::isinf(in[j])) return fail(h, NTC_ERR_ARG, "factor entries must be finite and >= 0");
-    NTC_CUDA(h, cudaMemsetAsync(h->U[mode].p, 0, sizeof(float) * h->dims[mode] * h->rp, h->stream));
-    NTC_CUDA(h, cudaMemcpy2DAsync(h->U[mode].p, sizeof(float) * h->rp, in, sizeof(float) * h->rank,
-                                  sizeof(float) * h->rank, (size_t)h->dims[mode], cudaMemcpyHostToDevice, h->stream));
-    if (h->storage_bf16) {
-        const int64_t m = h->dims[mode] * h->rp;
-        k_to_bf16<<<grid_for(m), 256, 0, h->stream>>>(h->U[mode].as<float>(), h->Ub[mode].as<uint16_t>(), m);
-        NTC_CUDA(h, cudaGetLastError());
-    }
-    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    ntc_status st = upload_factor(h, mode, in);
+    if (st != NTC_OK) return st;
     h->factor_set[mode] = true;
     return NTC_OK;
 }

@@ -114,13 +114,15 @@ struct ModeArgs {
     // mode order with `mode` left out; row stride rp elements
     const void* other[kMaxOrder - 1];
     int n_other;
+    int nhot;                 // storage rows 0..nhot-1 of every other mode are its most frequent rows
     int rank;        // R
     int rp;          // padded row length (8, 16, 32, 64)
     float lambda;
     double lambda_d;
     int power_iters;
     // updated mode
-    float* U;                 // float32 master A_l, [I][rp]
+    float* U;                 // float32 master A_l, [I][rp] in storage-row order
+    const int32_t* inv_self;  // original row -> storage row of the updated mode
     uint16_t* Ub;             // bfloat16 copy (or null)
     float* Y;                 // extrapolation buffer Y_l (null when MAX_INNER = 1)
     int read_y;               // 1: gradient point Y_l read from Y, 0: from U (l = 0)
