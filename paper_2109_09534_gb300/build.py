@@ -1,6 +1,11 @@
-"""Build the CUDA library ``libntc.so`` in-tree for sm_103a with nvcc."""
+"""Build the CUDA library ``libntc.so`` in-tree for sm_103a with nvcc.
+
+Each translation unit under csrc/ compiles to an object in parallel, then
+nvcc links the shared library.
+"""
 from __future__ import annotations
 
+import concurrent.futures as cf
 import glob
 import os
 import subprocess
@@ -8,32 +13,47 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libntc.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-         "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math", "-shared"]
+         "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math"]
 
 
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _deps():
+    return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
+        [os.path.join(ROOT, "include", "ntc.h")]
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "ntc.h")]
-    return any(os.path.getmtime(d) > t for d in deps)
+    return any(os.path.getmtime(d) > t for d in _deps())
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ into one shared library; returns its path."""
+    """Compile every .cu under csrc/ and link libntc.so; returns its path."""
     if not force and not _stale():
         return LIB
-    cmd = [NVCC, *FLAGS, *sources(), "-o", LIB + ".tmp"]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.check_call(cmd)
+    os.makedirs(OBJ, exist_ok=True)
+    objs = []
+    cmds = []
+    for src in sources():
+        obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+        objs.append(obj)
+        cmds.append([NVCC, *FLAGS, "-c", src, "-o", obj])
+    with cf.ThreadPoolExecutor(max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+        for cmd, fut in zip(cmds, [ex.submit(subprocess.check_call, c) for c in cmds]):
+            if verbose:
+                print(" ".join(cmd))
+            fut.result()
+    link = [NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs, "-o", LIB + ".tmp"]
+    subprocess.check_call(link)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -1,0 +1,91 @@
+// launch_rp.cuh -- enqueue one inner iteration of Algorithm 1 on one mode for
+// a given padded rank: light rows (side stream) and split rows (sample,
+// resolve, Gram partials, reduce, finish).  Included once per rank by
+// nmc_rp*.cu so that the instantiations compile in parallel.
+#pragma once
+
+#include "nmc_kernels.cuh"
+#include "ntc_host.h"
+
+namespace ntc {
+
+template <int RP, int EW, bool BF, int NOR>
+cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, bool mask_only) {
+    cudaStream_t s = L.s;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e;
+        constexpr int nomax = Gram<RP, EW, BF>::NOMAX;
+        if ((e = set_smem(k_light<RP, EW, BF, NOR>, LightSmem<RP, EW, BF, NOR>::bytes(nomax))) != cudaSuccess) return e;
+        if ((e = set_smem(k_heavy_gram<RP, EW, BF, NOR>, HeavyGramSmem<RP, EW, BF, NOR>::bytes(nomax))) != cudaSuccess)
+            return e;
+        if ((e = set_smem(k_heavy_finish<RP>, heavy_finish_smem<RP>())) != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaError_t e = cudaSuccess;
+    const bool fork = p.n_light > 0 && p.n_heavy > 0 && L.h->overlap;
+    if (fork) {
+        ntc_handle* h = L.h;
+        if (!h->side) {
+            if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+    }
+    if (p.n_light > 0) {
+        const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv + (int64_t)p.n_light * L.bpr;
+        cudaStream_t ls = fork ? L.h->side : s;
+        e = L.run_on(ls, NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
+            k_light<RP, EW, BF, NOR><<<p.n_light, kThreads, LightSmem<RP, EW, BF, NOR>::bytes(a.n_other), ls>>>(a);
+        });
+        if (e != cudaSuccess) return e;
+        if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;
+    }
+    if (p.n_heavy > 0) {
+        e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
+        if (e != cudaSuccess) return e;
+        e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_heavy_sample<EW><<<p.n_chunks, kThreads, 0, s>>>(a); });
+        if (e != cudaSuccess) return e;
+        e = L.run(NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<EW><<<p.n_heavy, kThreads, 0, s>>>(a); });
+        if (e != cudaSuccess) return e;
+        if (mask_only) {
+            k_heavy_mask<EW><<<p.n_chunks + p.n_heavy, kThreads, 0, s>>>(a);
+            ++*L.launches;
+        } else {
+            e = L.run(NTC_K_HEAVY_GRAM, p.visits_heavy * L.bpv, [&] {
+                k_heavy_gram<RP, EW, BF, NOR><<<p.n_chunks + p.n_heavy, kThreads,
+                                           HeavyGramSmem<RP, EW, BF, NOR>::bytes(a.n_other), s>>>(a);
+            });
+            if (e != cudaSuccess) return e;
+            e = L.run(NTC_K_HEAVY_FINISH, (int64_t)p.n_heavy * L.bpr, [&] {
+                k_heavy_reduce<RP><<<p.n_groups, kThreads, 0, s>>>(a);
+                k_heavy_finish<RP><<<p.n_heavy, kThreads, heavy_finish_smem<RP>(), s>>>(a);
+            });
+            ++*L.launches;
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (fork && (e = cudaStreamWaitEvent(s, L.h->ev_join, 0)) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// Orders 2-4 take the register-row Gram with the number of other modes fixed
+// at compile time; orders 5-8 stage factor rows in shared memory.
+template <int RP, bool BF>
+cudaError_t launch_mode_bf(int ew, const ModeArgs& a, const ModePlan& p, Launcher& L, bool mo) {
+    if (ew == 8) return launch_mode_t<RP, 8, BF, 0>(a, p, L, mo);
+    switch (a.n_other) {
+        case 1: return launch_mode_t<RP, 4, BF, 1>(a, p, L, mo);
+        case 2: return launch_mode_t<RP, 4, BF, 2>(a, p, L, mo);
+        default: return launch_mode_t<RP, 4, BF, 3>(a, p, L, mo);
+    }
+}
+
+template <int RP>
+cudaError_t launch_mode_rp(int ew, bool bf, const ModeArgs& a, const ModePlan& p, Launcher& L, bool mo) {
+    return bf ? launch_mode_bf<RP, true>(ew, a, p, L, mo) : launch_mode_bf<RP, false>(ew, a, p, L, mo);
+}
+
+}  // namespace ntc

@@ -4,6 +4,8 @@
 // projected momentum step.  Instantiated from nmc.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "ntc_internal.cuh"
 
 namespace ntc {
@@ -110,7 +112,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // the FMA pass of tile t and the product pass of tile t+1 while the factor
 // rows of tiles t+2, t+3 and the entries of tiles t+4, t+5 are in flight and
 // the bucket positions of tile t+6 are loaded into registers.
-template <int RP, int EW, bool BF16, int NT = kThreads, int NHOT = 0>
+template <int RP, int EW, bool BF16, int NT = kThreads, int NHOT = 0, int NOR = 0>
 struct Gram {
     static constexpr int T = RP / 8;
     static constexpr int NP = T * (T + 1) / 2;
@@ -133,14 +135,19 @@ struct Gram {
     static constexpr int VT_MAX = 200000 / BPV_MAX;
     static constexpr int VT0 = VT_BUDGET < VT_MAX ? VT_BUDGET : VT_MAX;
     static constexpr int VT1 = VT0 >= NG ? (VT0 / NG) * NG : VT0;
-    static constexpr int VT = VT1 > NT ? NT : (VT1 < 1 ? 1 : VT1);     // visits per staged tile
+    static constexpr int VTS = VT1 > NT ? NT : (VT1 < 1 ? 1 : VT1);
+    // With NOR > 0 other modes known at compile time, factor rows go straight
+    // to registers (RS product slots of one float4 per row per thread) one
+    // tile ahead instead of through shared memory.
+    static constexpr int RS = 2;
+    static constexpr int VT = NOR > 0 ? RS * NT / QPV : VTS;          // visits per staged tile
     static constexpr int VPG = (VT + NG - 1) / NG;    // visits per group per tile
     static constexpr int PW = NP * 64 + RP;           // reduced floats: the tiles, then b
     static constexpr int RED_BYTES = (NACT * 64 + NT * 4) * 4;
     static_assert(NT % QPV == 0, "a thread's product-pass quad must be fixed");
 
     __host__ __device__ static constexpr size_t pipe_bytes(int no) {
-        return (size_t)SR * no * VT * RST + (size_t)SE * VT * ENTB + (size_t)2 * VT * KST * 4;
+        return (NOR > 0 ? 0 : (size_t)SR * no * VT * RST) + (size_t)SE * VT * ENTB + (size_t)2 * VT * KST * 4;
     }
     // the most frequent NHOT rows of each other mode, resident for the block
     __host__ __device__ static constexpr size_t hot_bytes(int no) { return (size_t)no * NHOT * RST; }
@@ -210,6 +217,55 @@ struct Gram {
         }
     }
 
+    using RowT = typename std::conditional<BF16, uint2, float4>::type;   // 4 factor elements
+    __device__ __forceinline__ static float4 to_f4(const float4& v) { return v; }
+    __device__ __forceinline__ static float4 to_f4(const uint2& v) { return bf16x4_to_f32(v); }
+
+    // Register path: this thread's RS product slots of a tile -- the four
+    // factor elements of each other mode's row -- loaded through L1.
+    __device__ __forceinline__ void load_rows_reg(const ModeArgs& a, const Entry<EW>* ents, int nv,
+                                                  RowT (&rb)[RS][NOR > 0 ? NOR : 1]) {
+#pragma unroll
+        for (int j = 0; j < RS; ++j) {
+            const int s = threadIdx.x + j * NT;
+            if (s < nv * QPV) {
+                const int v = s / QPV, q = s % QPV;
+#pragma unroll
+                for (int o = 0; o < NOR; ++o) {
+                    const unsigned char* src = static_cast<const unsigned char*>(a.other[o]) +
+                                               (size_t)ents[v].w[o] * ROWB + q * (int)sizeof(RowT);
+                    rb[j][o] = __ldg(reinterpret_cast<const RowT*>(src));
+                }
+            }
+        }
+    }
+
+    __device__ __forceinline__ void product_reg(const Entry<EW>* ents, float* kt, int nv,
+                                                const RowT (&rb)[RS][NOR > 0 ? NOR : 1]) {
+#pragma unroll
+        for (int j = 0; j < RS; ++j) {
+            const int s = threadIdx.x + j * NT;
+            if (s < nv * QPV) {
+                const int v = s / QPV, q = s % QPV;
+                float4 p = to_f4(rb[j][0]);
+#pragma unroll
+                for (int o = 1; o < NOR; ++o) {
+                    const float4 u = to_f4(rb[j][o]);
+                    p.x *= u.x;
+                    p.y *= u.y;
+                    p.z *= u.z;
+                    p.w *= u.w;
+                }
+                *reinterpret_cast<float4*>(kt + v * KST + 4 * q) = p;
+                const float x = __int_as_float(ents[v].w[EW - 1]);
+                bq.x = fmaf(x, p.x, bq.x);
+                bq.y = fmaf(x, p.y, bq.y);
+                bq.z = fmaf(x, p.z, bq.z);
+                bq.w = fmaf(x, p.w, bq.w);
+            }
+        }
+    }
+
     __device__ __forceinline__ void accumulate(const float* kt, int nv) {
         if (!active) return;
 #pragma unroll
@@ -234,6 +290,10 @@ struct Gram {
     // holds region_bytes(no) bytes of shared memory.
     template <class GetPos>
     __device__ __forceinline__ void run(const ModeArgs& a, const GetPos& getpos, int nvis, unsigned char* pipe) {
+        if constexpr (NOR > 0) {
+            run_reg(a, getpos, nvis, pipe);
+            return;
+        }
         const int no = a.n_other;
         const int tid = threadIdx.x;
         unsigned char* hot = pipe + region_bytes(no);                                   // [no][NHOT][RST]
@@ -314,6 +374,60 @@ struct Gram {
             issue_rows(t + 3);
             issue_entries(t + 5, pos_next);
             pos_next = pos_of(t + 6);
+            cp_async_commit();
+            accumulate(ktile + (t & 1) * VT * KST, tile_n(t));
+            __syncthreads();
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+
+    // Register-path pipeline: iteration t forms the k-tile of t+1 from the rows
+    // in registers, loads the rows of t+2 into them, copies the entries of t+4
+    // and accumulates tile t.
+    template <class GetPos>
+    __device__ __forceinline__ void run_reg(const ModeArgs& a, const GetPos& getpos, int nvis, unsigned char* pipe) {
+        const int tid = threadIdx.x;
+        Entry<EW>* ents = reinterpret_cast<Entry<EW>*>(pipe);                          // [SE][VT]
+        float* ktile = reinterpret_cast<float*>(pipe + (size_t)SE * VT * ENTB);        // [2][VT][KST]
+        const Entry<EW>* bucket = reinterpret_cast<const Entry<EW>*>(a.bucket);
+        const int ntiles = (nvis + VT - 1) / VT;
+        auto tile_n = [&](int t) { return min(VT, nvis - t * VT); };
+        auto pos_of = [&](int t) -> uint32_t {
+            return (t < ntiles && tid < tile_n(t)) ? getpos(t * VT + tid) : 0u;
+        };
+        auto issue_entries = [&](int t, uint32_t pos) {
+            if (t < ntiles && tid < tile_n(t)) {
+                const unsigned char* src = reinterpret_cast<const unsigned char*>(bucket + pos);
+                unsigned char* dst = reinterpret_cast<unsigned char*>(ents + (t % SE) * VT + tid);
+#pragma unroll
+                for (int c = 0; c < ENTB / 16; ++c) cp_async16(dst + 16 * c, src + 16 * c);
+            }
+        };
+        RowT rb[RS][NOR > 0 ? NOR : 1];
+        issue_entries(0, pos_of(0));
+        issue_entries(1, pos_of(1));
+        issue_entries(2, pos_of(2));
+        cp_async_commit();
+        const uint32_t p3 = pos_of(3);
+        cp_async_wait<0>();
+        __syncthreads();
+        if (ntiles > 0) {
+            load_rows_reg(a, ents, tile_n(0), rb);
+            product_reg(ents, ktile, tile_n(0), rb);
+        }
+        if (ntiles > 1) load_rows_reg(a, ents + VT, tile_n(1), rb);
+        issue_entries(3, p3);
+        cp_async_commit();
+        uint32_t pos_next = pos_of(4);
+        for (int t = 0; t < ntiles; ++t) {
+            cp_async_wait<1>();      // entries of t+2
+            __syncthreads();
+            if (t + 1 < ntiles) product_reg(ents + ((t + 1) % SE) * VT, ktile + ((t + 1) & 1) * VT * KST,
+                                            tile_n(t + 1), rb);
+            if (t + 2 < ntiles) load_rows_reg(a, ents + ((t + 2) % SE) * VT, tile_n(t + 2), rb);
+            issue_entries(t + 4, pos_next);
+            pos_next = pos_of(t + 5);
             cp_async_commit();
             accumulate(ktile + (t & 1) * VT * KST, tile_n(t));
             __syncthreads();
@@ -493,9 +607,9 @@ __device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float
 // shared memory, exact k-subset selection, Gram/data reduction, row update.
 // Shared memory: [visit list u16 x kLightMax | union(keys, Gram pipeline,
 // reduction)] + reduced sums, H, b, vectors, histogram.
-template <int RP, int EW, bool BF16>
+template <int RP, int EW, bool BF16, int NOR>
 struct LightSmem {
-    using G = Gram<RP, EW, BF16>;
+    using G = Gram<RP, EW, BF16, kThreads, 0, NOR>;
     static constexpr size_t VIS = kLightMax * 2;
     static constexpr size_t KEYS = kLightMax * 4;
     __host__ __device__ static constexpr size_t union_bytes(int no) {
@@ -505,10 +619,10 @@ struct LightSmem {
     __host__ __device__ static constexpr size_t bytes(int no) { return VIS + union_bytes(no) + TAIL; }
 };
 
-template <int RP, int EW, bool BF16>
+template <int RP, int EW, bool BF16, int NOR>
 __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
-    using G = Gram<RP, EW, BF16>;
-    using S = LightSmem<RP, EW, BF16>;
+    using G = Gram<RP, EW, BF16, kThreads, 0, NOR>;
+    using S = LightSmem<RP, EW, BF16, NOR>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int no = a.n_other;
     uint16_t* vis = reinterpret_cast<uint16_t*>(smem_raw);
@@ -736,15 +850,15 @@ struct HotRows {
     static constexpr int value = 0;
 };
 
-template <int RP, int EW, bool BF16>
+template <int RP, int EW, bool BF16, int NOR>
 struct HeavyGramSmem {
-    using G = Gram<RP, EW, BF16, kGramThreads, HotRows<RP>::value>;
+    using G = Gram<RP, EW, BF16, kGramThreads, HotRows<RP>::value, NOR>;
     __host__ __device__ static constexpr size_t bytes(int no) { return G::total_bytes(no) + (size_t)G::PW * 4; }
 };
 
-template <int RP, int EW, bool BF16>
+template <int RP, int EW, bool BF16, int NOR>
 __global__ void __launch_bounds__(kGramThreads, 2) k_heavy_gram(ModeArgs a) {
-    using G = Gram<RP, EW, BF16, kGramThreads, HotRows<RP>::value>;
+    using G = Gram<RP, EW, BF16, kGramThreads, HotRows<RP>::value, NOR>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* pipe = smem_raw;
     float* red = reinterpret_cast<float*>(smem_raw);
@@ -772,7 +886,6 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_heavy_gram(ModeArgs a) {
 // Heavy rows, step 4a: a row's items (its chunks in order, then its chosen
 // candidates) are summed in fixed groups of kReduceGroup consecutive items,
 // one block per group, so that long rows are not summed by a single block.
-constexpr int kReduceGroup = 16;
 
 template <int RP>
 __global__ void __launch_bounds__(kThreads) k_heavy_reduce(ModeArgs a) {
@@ -829,6 +942,7 @@ __global__ void __launch_bounds__(kThreads) k_heavy_finish(ModeArgs a) {
 }
 
 // Sampler-only mode for heavy rows: mark the chosen positions.
+template <int EW>
 __global__ void k_heavy_mask(ModeArgs a) {
     const int item = blockIdx.x;
     const uint32_t* list;

@@ -13,116 +13,10 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ntc.h"
 #include "aux_kernels.cuh"
-#include "nmc_kernels.cuh"
+#include "ntc_host.h"
 
 using namespace ntc;
-
-namespace {
-
-struct DevMem {
-    void* p = nullptr;
-    size_t bytes = 0;
-    DevMem() = default;
-    DevMem(const DevMem&) = delete;
-    DevMem& operator=(const DevMem&) = delete;
-    ~DevMem() { release(); }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    // grow-only; contents are not preserved
-    cudaError_t ensure(size_t b) {
-        if (b <= bytes && p) return cudaSuccess;
-        release();
-        if (b == 0) b = 16;
-        cudaError_t e = cudaMalloc(&p, b);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            return e;
-        }
-        bytes = b;
-        return cudaSuccess;
-    }
-    template <class T>
-    T* as() const { return static_cast<T*>(p); }
-};
-
-struct ModePlan {
-    bool valid = false;
-    double c = 0.0;
-    int heavy_threshold = 0, chunk = 0;
-    double bracket_z = 0.0;
-    int64_t visits = 0, visits_heavy = 0, rows_updated = 0, rows_skipped = 0;
-    int n_light = 0, n_heavy = 0, n_chunks = 0;
-    int64_t cand_total = 0, extra_total = 0;
-    int n_groups = 0;
-    DevMem light_rows, light_k, chunks, chunk_caps, heavy, bracket, heavy_cand, groups, heavy_groups;
-};
-
-int pad_rank(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
-
-}  // namespace
-
-struct ntc_handle {
-    int order = 0;
-    int64_t dims[kMaxOrder] = {};
-    int rank = 0, rp = 0;
-    double lambda = 0.0;
-    // parameters
-    int max_inner = 1, power_iters = 10, storage_bf16 = 0, keep_perm = 0;
-    uint64_t init_seed = 3;
-    double bracket_z = 7.0;
-    int heavy_threshold = 4096, chunk = 16384;
-    cudaStream_t stream = nullptr;
-    // light rows run on a side stream beside the split-row kernels of the same
-    // mode update (they write disjoint rows); fork/join through two events
-    int overlap = 1;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    int device = 0;
-    // state
-    uint64_t ao_iter = 0;
-    int64_t nnz = -1;
-    bool factor_set[kMaxOrder] = {};
-    std::string err;
-    ntc_stats stats = {};
-    // device data
-    DevMem U[kMaxOrder], Ub[kMaxOrder], Y;
-    DevMem row_ptr[kMaxOrder], bucket[kMaxOrder], perm[kMaxOrder];
-    // Factor rows are stored in descending order of their mode's observation
-    // counts (storage row = inv[original row], original row = rows[storage row]),
-    // so that the most frequent rows of a mode are its first storage rows.
-    // Identity until observations are set.  Bucket positions keep original order.
-    DevMem inv_dev[kMaxOrder], rows_dev[kMaxOrder];
-    std::vector<int32_t> inv_h[kMaxOrder], rows_h[kMaxOrder];
-    DevMem coo_idx, coo_val, dims_dev;
-    std::vector<int64_t> row_ptr_h[kMaxOrder];
-    ModePlan plan[kMaxOrder];
-    // scratch
-    DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, partial2, stat, red, mask;
-    // per-kernel event timing ("profile")
-    int profile = 0;
-    struct Pending {
-        int kind;
-        int64_t bytes;
-        cudaEvent_t a, b;
-    };
-    std::vector<Pending> pending;
-    double prof_ms[NTC_K_COUNT] = {};
-    int64_t prof_launches[NTC_K_COUNT] = {}, prof_bytes[NTC_K_COUNT] = {};
-    ~ntc_handle() {
-        for (auto& q : pending) {
-            cudaEventDestroy(q.a);
-            cudaEventDestroy(q.b);
-        }
-        if (side) cudaStreamDestroy(side);
-        if (ev_fork) cudaEventDestroy(ev_fork);
-        if (ev_join) cudaEventDestroy(ev_join);
-    }
-};
 
 namespace {
 
@@ -147,109 +41,6 @@ int grid_for(int64_t n, int per_block = 256, int cap = 152 * 16) {
     if (g < 1) g = 1;
     if (g > cap) g = cap;
     return (int)g;
-}
-
-// ---- one-time smem attributes per kernel instantiation --------------------
-template <class K>
-cudaError_t set_smem(K kernel, size_t bytes) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// ---- mode update launches ---------------------------------------------------
-// Enqueues one kernel; with profiling on, brackets it with a pair of events.
-struct Launcher {
-    ntc_handle* h;
-    cudaStream_t s;
-    int64_t* launches;
-    int64_t bpv, bpr;   // algorithmic bytes per visit and per row update
-    template <class F>
-    cudaError_t run(int kind, int64_t bytes, F&& f) { return run_on(s, kind, bytes, f); }
-    template <class F>
-    cudaError_t run_on(cudaStream_t s, int kind, int64_t bytes, F&& f) {
-        cudaEvent_t a = nullptr, b = nullptr;
-        if (h->profile) {
-            cudaError_t e = cudaEventCreate(&a);
-            if (e == cudaSuccess) e = cudaEventCreate(&b);
-            if (e == cudaSuccess) e = cudaEventRecord(a, s);
-            if (e != cudaSuccess) return e;
-        }
-        f();
-        ++*launches;
-        if (h->profile) {
-            cudaError_t e = cudaEventRecord(b, s);
-            if (e != cudaSuccess) return e;
-            h->pending.push_back({kind, bytes, a, b});
-        }
-        return cudaSuccess;
-    }
-};
-
-template <int RP, int EW, bool BF>
-cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, bool mask_only) {
-    cudaStream_t s = L.s;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e;
-        constexpr int nomax = Gram<RP, EW, BF>::NOMAX;
-        if ((e = set_smem(k_light<RP, EW, BF>, LightSmem<RP, EW, BF>::bytes(nomax))) != cudaSuccess) return e;
-        if ((e = set_smem(k_heavy_gram<RP, EW, BF>, HeavyGramSmem<RP, EW, BF>::bytes(nomax))) != cudaSuccess)
-            return e;
-        if ((e = set_smem(k_heavy_finish<RP>, heavy_finish_smem<RP>())) != cudaSuccess) return e;
-        attr = true;
-    }
-    cudaError_t e = cudaSuccess;
-    const bool fork = p.n_light > 0 && p.n_heavy > 0 && L.h->overlap;
-    if (fork) {
-        ntc_handle* h = L.h;
-        if (!h->side) {
-            if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return e;
-            if ((e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
-            if ((e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
-        }
-        if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
-    }
-    if (p.n_light > 0) {
-        const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv + (int64_t)p.n_light * L.bpr;
-        cudaStream_t ls = fork ? L.h->side : s;
-        e = L.run_on(ls, NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
-            k_light<RP, EW, BF><<<p.n_light, kThreads, LightSmem<RP, EW, BF>::bytes(a.n_other), ls>>>(a);
-        });
-        if (e != cudaSuccess) return e;
-        if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;
-    }
-    if (p.n_heavy > 0) {
-        e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
-        if (e != cudaSuccess) return e;
-        e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_heavy_sample<EW><<<p.n_chunks, kThreads, 0, s>>>(a); });
-        if (e != cudaSuccess) return e;
-        e = L.run(NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<EW><<<p.n_heavy, kThreads, 0, s>>>(a); });
-        if (e != cudaSuccess) return e;
-        if (mask_only) {
-            k_heavy_mask<<<p.n_chunks + p.n_heavy, kThreads, 0, s>>>(a);
-            ++*L.launches;
-        } else {
-            e = L.run(NTC_K_HEAVY_GRAM, p.visits_heavy * L.bpv, [&] {
-                k_heavy_gram<RP, EW, BF><<<p.n_chunks + p.n_heavy, kThreads,
-                                           HeavyGramSmem<RP, EW, BF>::bytes(a.n_other), s>>>(a);
-            });
-            if (e != cudaSuccess) return e;
-            e = L.run(NTC_K_HEAVY_FINISH, (int64_t)p.n_heavy * L.bpr, [&] {
-                k_heavy_reduce<RP><<<p.n_groups, kThreads, 0, s>>>(a);
-                k_heavy_finish<RP><<<p.n_heavy, kThreads, heavy_finish_smem<RP>(), s>>>(a);
-            });
-            ++*L.launches;
-            if (e != cudaSuccess) return e;
-        }
-    }
-    if (fork && (e = cudaStreamWaitEvent(s, L.h->ev_join, 0)) != cudaSuccess) return e;
-    return cudaGetLastError();
-}
-
-template <int RP>
-cudaError_t launch_mode_rp(int ew, bool bf, const ModeArgs& a, const ModePlan& p, Launcher& L, bool mo) {
-    if (ew == 4) return bf ? launch_mode_t<RP, 4, true>(a, p, L, mo) : launch_mode_t<RP, 4, false>(a, p, L, mo);
-    return bf ? launch_mode_t<RP, 8, true>(a, p, L, mo) : launch_mode_t<RP, 8, false>(a, p, L, mo);
 }
 
 cudaError_t launch_mode(int rp, int ew, bool bf, const ModeArgs& a, const ModePlan& p, Launcher& L, bool mo) {

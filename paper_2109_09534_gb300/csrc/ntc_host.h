@@ -1,0 +1,163 @@
+// ntc_host.h -- host-side types shared by the C ABI implementation
+// (ntc_api.cu) and the per-rank launch units (nmc_rp*.cu): device buffers,
+// the per-(mode, c) work plan, the handle, and the kernel launcher.
+#pragma once
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ntc.h"
+#include "ntc_internal.cuh"
+
+namespace ntc {
+
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    ~DevMem() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // grow-only; contents are not preserved
+    cudaError_t ensure(size_t b) {
+        if (b <= bytes && p) return cudaSuccess;
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = b;
+        return cudaSuccess;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct ModePlan {
+    bool valid = false;
+    double c = 0.0;
+    int heavy_threshold = 0, chunk = 0;
+    double bracket_z = 0.0;
+    int64_t visits = 0, visits_heavy = 0, rows_updated = 0, rows_skipped = 0;
+    int n_light = 0, n_heavy = 0, n_chunks = 0;
+    int64_t cand_total = 0, extra_total = 0;
+    int n_groups = 0;
+    DevMem light_rows, light_k, chunks, chunk_caps, heavy, bracket, heavy_cand, groups, heavy_groups;
+};
+
+inline int pad_rank(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
+
+}  // namespace ntc
+
+struct ntc_handle {
+    int order = 0;
+    int64_t dims[ntc::kMaxOrder] = {};
+    int rank = 0, rp = 0;
+    double lambda = 0.0;
+    // parameters
+    int max_inner = 1, power_iters = 10, storage_bf16 = 0, keep_perm = 0;
+    uint64_t init_seed = 3;
+    double bracket_z = 7.0;
+    int heavy_threshold = 4096, chunk = 16384;
+    cudaStream_t stream = nullptr;
+    // light rows run on a side stream beside the split-row kernels of the same
+    // mode update (they write disjoint rows); fork/join through two events
+    int overlap = 1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int device = 0;
+    // state
+    uint64_t ao_iter = 0;
+    int64_t nnz = -1;
+    bool factor_set[ntc::kMaxOrder] = {};
+    std::string err;
+    ntc_stats stats = {};
+    // device data
+    ntc::DevMem U[ntc::kMaxOrder], Ub[ntc::kMaxOrder], Y;
+    ntc::DevMem row_ptr[ntc::kMaxOrder], bucket[ntc::kMaxOrder], perm[ntc::kMaxOrder];
+    // Factor rows are stored in descending order of their mode's observation
+    // counts (storage row = inv[original row], original row = rows[storage row]),
+    // so that the most frequent rows of a mode are its first storage rows.
+    // Identity until observations are set.  Bucket positions keep original order.
+    ntc::DevMem inv_dev[ntc::kMaxOrder], rows_dev[ntc::kMaxOrder];
+    std::vector<int32_t> inv_h[ntc::kMaxOrder], rows_h[ntc::kMaxOrder];
+    ntc::DevMem coo_idx, coo_val, dims_dev;
+    std::vector<int64_t> row_ptr_h[ntc::kMaxOrder];
+    ntc::ModePlan plan[ntc::kMaxOrder];
+    // scratch
+    ntc::DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, partial2, stat, red, mask;
+    // per-kernel event timing ("profile")
+    int profile = 0;
+    struct Pending {
+        int kind;
+        int64_t bytes;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    double prof_ms[NTC_K_COUNT] = {};
+    int64_t prof_launches[NTC_K_COUNT] = {}, prof_bytes[NTC_K_COUNT] = {};
+    ~ntc_handle() {
+        for (auto& q : pending) {
+            cudaEventDestroy(q.a);
+            cudaEventDestroy(q.b);
+        }
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+    }
+};
+
+
+namespace ntc {
+
+// ---- one-time smem attributes per kernel instantiation --------------------
+template <class K>
+inline cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---- mode update launches ---------------------------------------------------
+// Enqueues one kernel; with profiling on, brackets it with a pair of events.
+struct Launcher {
+    ntc_handle* h;
+    cudaStream_t s;
+    int64_t* launches;
+    int64_t bpv, bpr;   // algorithmic bytes per visit and per row update
+    template <class F>
+    cudaError_t run(int kind, int64_t bytes, F&& f) { return run_on(s, kind, bytes, f); }
+    template <class F>
+    cudaError_t run_on(cudaStream_t s, int kind, int64_t bytes, F&& f) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (h->profile) {
+            cudaError_t e = cudaEventCreate(&a);
+            if (e == cudaSuccess) e = cudaEventCreate(&b);
+            if (e == cudaSuccess) e = cudaEventRecord(a, s);
+            if (e != cudaSuccess) return e;
+        }
+        f();
+        ++*launches;
+        if (h->profile) {
+            cudaError_t e = cudaEventRecord(b, s);
+            if (e != cudaSuccess) return e;
+            h->pending.push_back({kind, bytes, a, b});
+        }
+        return cudaSuccess;
+    }
+};
+
+template <int RP>
+cudaError_t launch_mode_rp(int ew, bool bf, const ModeArgs& a, const ModePlan& p, Launcher& L, bool mask_only);
+extern template cudaError_t launch_mode_rp<8>(int, bool, const ModeArgs&, const ModePlan&, Launcher&, bool);
+extern template cudaError_t launch_mode_rp<16>(int, bool, const ModeArgs&, const ModePlan&, Launcher&, bool);
+extern template cudaError_t launch_mode_rp<32>(int, bool, const ModeArgs&, const ModePlan&, Launcher&, bool);
+extern template cudaError_t launch_mode_rp<64>(int, bool, const ModeArgs&, const ModePlan&, Launcher&, bool);
+
+}  // namespace ntc

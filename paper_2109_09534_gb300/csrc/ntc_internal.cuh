@@ -11,6 +11,7 @@ namespace ntc {
 constexpr int kMaxOrder = 8;
 constexpr int kThreads = 256;        // threads per block of every row/chunk kernel
 constexpr int kLightMax = 4096;      // largest row whose keys fit in shared memory
+constexpr int kReduceGroup = 16;     // split-row partials summed per block of the group reduction
 
 // Bucket entry of one observation, seen from the mode being updated: the other
 // modes' indices in increasing mode order, then the value in the last word.
