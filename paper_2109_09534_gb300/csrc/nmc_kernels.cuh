@@ -112,7 +112,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // the FMA pass of tile t and the product pass of tile t+1 while the factor
 // rows of tiles t+2, t+3 and the entries of tiles t+4, t+5 are in flight and
 // the bucket positions of tile t+6 are loaded into registers.
-template <int RP, int EW, bool BF16, int NT = kThreads, int NHOT = 0, int NOR = 0>
+template <int RP, int EW, bool BF16, int NT = kThreads, int NHOT = 0, int NOR = 0, int RREG = 32>
 struct Gram {
     static constexpr int T = RP / 8;
     static constexpr int NP = T * (T + 1) / 2;
@@ -137,10 +137,11 @@ struct Gram {
     static constexpr int VT1 = VT0 >= NG ? (VT0 / NG) * NG : VT0;
     static constexpr int VTS = VT1 > NT ? NT : (VT1 < 1 ? 1 : VT1);
     // With NOR > 0 other modes known at compile time, factor rows go straight
-    // to registers (RS product slots of one float4 per row per thread) one
-    // tile ahead instead of through shared memory.
-    static constexpr int RS = 2;
-    static constexpr int VT = NOR > 0 ? RS * NT / QPV : VTS;          // visits per staged tile
+    // to registers (RS product slots of four elements per row per thread, about
+    // RREG registers) one tile ahead instead of through shared memory.
+    static constexpr int RS0 = NOR > 0 ? RREG / (NOR * (BF16 ? 2 : 4)) : 1;
+    static constexpr int RS = RS0 < 1 ? 1 : (RS0 > 4 ? 4 : RS0);
+    static constexpr int VT = NOR > 0 ? (RS * NT / QPV < NT ? RS * NT / QPV : NT) : VTS;   // visits per tile
     static constexpr int VPG = (VT + NG - 1) / NG;    // visits per group per tile
     static constexpr int PW = NP * 64 + RP;           // reduced floats: the tiles, then b
     static constexpr int RED_BYTES = (NACT * 64 + NT * 4) * 4;
@@ -609,7 +610,7 @@ __device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float
 // reduction)] + reduced sums, H, b, vectors, histogram.
 template <int RP, int EW, bool BF16, int NOR>
 struct LightSmem {
-    using G = Gram<RP, EW, BF16, kThreads, 0, NOR>;
+    using G = Gram<RP, EW, BF16, kThreads, 0, NOR, 24>;
     static constexpr size_t VIS = kLightMax * 2;
     static constexpr size_t KEYS = kLightMax * 4;
     __host__ __device__ static constexpr size_t union_bytes(int no) {
@@ -621,7 +622,7 @@ struct LightSmem {
 
 template <int RP, int EW, bool BF16, int NOR>
 __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
-    using G = Gram<RP, EW, BF16, kThreads, 0, NOR>;
+    using G = Gram<RP, EW, BF16, kThreads, 0, NOR, 24>;
     using S = LightSmem<RP, EW, BF16, NOR>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int no = a.n_other;
