@@ -20,6 +20,7 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         if ((e = set_smem(k_heavy_gram<RP, EW, BF, NOR>, HeavyGramSmem<RP, EW, BF, NOR>::bytes(nomax))) != cudaSuccess)
             return e;
         if ((e = set_smem(k_heavy_finish<RP>, heavy_finish_smem<RP>())) != cudaSuccess) return e;
+        if ((e = set_smem(k_light_finish<RP>, LightFinish<RP>::bytes())) != cudaSuccess) return e;
         attr = true;
     }
     cudaError_t e = cudaSuccess;
@@ -39,6 +40,11 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         cudaStream_t ls = fork ? L.h->side : s;
         e = L.run_on(ls, NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
             k_light<RP, EW, BF, NOR><<<p.n_light, kThreads, LightSmem<RP, EW, BF, NOR>::bytes(a.n_other), ls>>>(a);
+            if (!mask_only) {
+                constexpr int W = LightFinish<RP>::WARPS;
+                k_light_finish<RP><<<(p.n_light + W - 1) / W, W * 32, LightFinish<RP>::bytes(), ls>>>(a);
+                ++*L.launches;
+            }
         });
         if (e != cudaSuccess) return e;
         if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;

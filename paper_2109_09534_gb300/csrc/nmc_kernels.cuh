@@ -79,6 +79,101 @@ __device__ unsigned long long block_select_kth(const Get& get, int n, int k, uns
 }
 
 // ---------------------------------------------------------------------------
+// Single-histogram select for the same problem when a monotone digit of the
+// composite spreads the items over kSelBins bins (uniform Philox keys do):
+// one histogram pass finds the bin that holds the m-th smallest item; if that
+// bin is not taken whole, its few members are ranked exactly.  Loads are
+// issued eight per thread before their histogram updates so that items read
+// from global memory are not a chain of dependent latencies.  Falls back to
+// block_select_kth when the boundary bin holds more than kSelCap items.
+//   digit(c) -> bin in [0, kSelBins), non-decreasing in c
+//   binmax(b) -> a composite >= every item of bins <= b and < every item of bins > b
+// Shared memory: hist kSelBins + 16 unsigned, mem kSelCap composites.
+constexpr int kSelBins = 4096;
+constexpr int kSelCap = 512;
+
+template <class Get, class Digit, class BinMax>
+__device__ unsigned long long block_select_digit(const Get& get, int n, int m, const Digit& digit,
+                                                 const BinMax& binmax, unsigned* hist,
+                                                 unsigned long long* mem, int* scan_tmp) {
+    constexpr int PER = kSelBins / kThreads;
+    static_assert(PER * kThreads == kSelBins && PER % 4 == 0, "bins per thread");
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kSelBins / 4; i += kThreads) reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) hist[kSelBins + 3] = 0u;
+    __syncthreads();
+    for (int base = 0; base < n; base += kThreads * 8) {
+        unsigned long long c[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = base + u * kThreads + tid;
+            c[u] = j < n ? get(j) : ~0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (c[u] != ~0ull) atomicAdd(&hist[digit(c[u])], 1u);
+    }
+    __syncthreads();
+    unsigned loc[PER];
+    int own = 0;
+#pragma unroll
+    for (int i = 0; i < PER; i += 4) {
+        const uint4 v = reinterpret_cast<const uint4*>(hist + tid * PER)[i / 4];
+        loc[i] = v.x;
+        loc[i + 1] = v.y;
+        loc[i + 2] = v.z;
+        loc[i + 3] = v.w;
+        own += (int)(v.x + v.y + v.z + v.w);
+    }
+    int total;
+    const int excl = block_exclusive_scan(own, scan_tmp, &total);
+    if (excl < m && m <= excl + own) {
+        int cum = excl;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            if (cum < m && m <= cum + (int)loc[i]) {
+                hist[kSelBins] = (unsigned)(tid * PER + i);   // bin
+                hist[kSelBins + 1] = (unsigned)cum;           // items below the bin
+                hist[kSelBins + 2] = loc[i];                  // items in the bin
+            }
+            cum += (int)loc[i];
+        }
+    }
+    __syncthreads();
+    const unsigned b = hist[kSelBins];
+    const int below = (int)hist[kSelBins + 1], cnt = (int)hist[kSelBins + 2];
+    const int need = m - below;   // 1 <= need <= cnt
+    if (need == cnt) return binmax(b);
+    if (cnt > kSelCap) {
+        __syncthreads();
+        return block_select_kth(get, n, m, hist);
+    }
+    for (int base = 0; base < n; base += kThreads * 8) {
+        unsigned long long c[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = base + u * kThreads + tid;
+            c[u] = j < n ? get(j) : ~0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (c[u] != ~0ull && digit(c[u]) == b) mem[atomicAdd(&hist[kSelBins + 3], 1u)] = c[u];
+    }
+    __syncthreads();
+    unsigned long long* res = reinterpret_cast<unsigned long long*>(hist + kSelBins + 4);   // 8-byte aligned
+    for (int t = tid; t < cnt; t += kThreads) {
+        const unsigned long long ct = mem[t];
+        int r = 0;
+        for (int u = 0; u < cnt; ++u) r += mem[u] < ct ? 1 : 0;
+        if (r == need - 1) *res = ct;
+    }
+    __syncthreads();
+    const unsigned long long T = *res;
+    __syncthreads();
+    return T;
+}
+
+// ---------------------------------------------------------------------------
 // 16-byte asynchronous global -> shared copies (cp.async, L1 bypassed).
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -299,7 +394,7 @@ struct Gram {
         const int tid = threadIdx.x;
         unsigned char* hot = pipe + region_bytes(no);                                   // [no][NHOT][RST]
         const int nhot = NHOT > 0 ? min(NHOT, a.nhot) : 0;
-        if (NHOT > 0) {
+        if constexpr (NHOT > 0) {
             for (int i = tid; i < no * nhot * CPR; i += NT) {
                 const int c = i % CPR, ro = i / CPR, r = ro % nhot, o = ro / nhot;
                 cp_async16_ca(hot + ((size_t)o * NHOT + r) * RST + 16 * c,
@@ -513,11 +608,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 // iteration count, Rayleigh quotient), projected step, momentum, extrapolation.
 // H is zero outside the leading R x R block, so loops run over RP.
 template <int RP>
-__device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float* H, const float* bvec,
-                                           float* vsh) {
-    if (threadIdx.x >= 32) return;
+__device__ __forceinline__ void finish_row_warp(const ModeArgs& a, int p, const float* H, const float* bvec,
+                                                float* vsh, int lane) {
     constexpr int PER = RP > 32 ? RP / 32 : 1;
-    const int lane = threadIdx.x;
     const int R = a.rank;
     const size_t base = (size_t)a.inv_self[p] * RP;
     float y[PER], al[PER], grad[PER], v[PER], w[PER];
@@ -603,6 +696,34 @@ __device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float
     }
 }
 
+template <int RP>
+__device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float* H, const float* bvec,
+                                           float* vsh) {
+    if (threadIdx.x < 32) finish_row_warp<RP>(a, p, H, bvec, vsh, threadIdx.x);
+}
+
+// build_H for one warp: the reduced tiles of one row (global memory) into the
+// warp's own H (stride RP+1) and b.
+template <int RP>
+__device__ __forceinline__ void build_H_warp(const float* sum, float* H, float* bvec, int R, float lambda,
+                                             int lane) {
+    constexpr int T = RP / 8, NP = T * (T + 1) / 2;
+    for (int s = lane; s < NP * 64; s += 32) {
+        const int p = s >> 6, ij = s & 63, i = ij >> 3, j = ij & 7;
+        int a, b;
+        pair_ab(T, p, &a, &b);
+        const int r = 8 * a + i, c = 8 * b + j;
+        if (a == b && i > j) continue;
+        const float v = sum[p * 64 + ij];
+        H[r * (RP + 1) + c] = v;
+        H[c * (RP + 1) + r] = v;
+    }
+    for (int r = lane; r < RP; r += 32) bvec[r] = sum[NP * 64 + r];
+    __syncwarp();
+    for (int r = lane; r < R; r += 32) H[r * (RP + 1) + r] += lambda;
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // Light rows (n_p <= kLightMax): one block per row does everything: keys in
 // shared memory, exact k-subset selection, Gram/data reduction, row update.
@@ -612,11 +733,13 @@ template <int RP, int EW, bool BF16, int NOR>
 struct LightSmem {
     using G = Gram<RP, EW, BF16, kThreads, 0, NOR, 24>;
     static constexpr size_t VIS = kLightMax * 2;
+    // keys, then the select's histogram and boundary-bin members
     static constexpr size_t KEYS = kLightMax * 4;
+    static constexpr size_t SEL = KEYS + (size_t)(kSelBins + 16) * 4 + (size_t)kSelCap * 8;
     __host__ __device__ static constexpr size_t union_bytes(int no) {
-        return G::region_bytes(no) > KEYS ? G::region_bytes(no) : KEYS;
+        return G::region_bytes(no) > SEL ? G::region_bytes(no) : SEL;
     }
-    static constexpr size_t TAIL = (size_t)(G::PW + RP * (RP + 1) + 2 * RP + 8 + 256 + 8 + 16) * 4;
+    static constexpr size_t TAIL = (size_t)(kThreads / 32 + 16) * 4;
     __host__ __device__ static constexpr size_t bytes(int no) { return VIS + union_bytes(no) + TAIL; }
 };
 
@@ -629,13 +752,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
     uint16_t* vis = reinterpret_cast<uint16_t*>(smem_raw);
     unsigned char* uni = smem_raw + S::VIS;
     uint32_t* keys = reinterpret_cast<uint32_t*>(uni);
+    unsigned* hist = reinterpret_cast<unsigned*>(uni + S::KEYS);
+    unsigned long long* mem = reinterpret_cast<unsigned long long*>(hist + kSelBins + 16);
     float* red = reinterpret_cast<float*>(uni);
-    float* sum = reinterpret_cast<float*>(uni + S::union_bytes(no));
-    float* H = sum + G::PW;
-    float* bvec = H + RP * (RP + 1);
-    float* vsh = bvec + RP;
-    unsigned* hist = reinterpret_cast<unsigned*>(vsh + RP + 8);
-    int* scan_tmp = reinterpret_cast<int*>(hist + 256 + 8);
+    int* scan_tmp = reinterpret_cast<int*>(uni + S::union_bytes(no));
 
     const int row = a.light_rows[blockIdx.x];
     const int k = a.light_k[blockIdx.x];
@@ -646,22 +766,41 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
     // Alg. 1 line 5: the k smallest (key, position) of the row's n positions
     unsigned long long T = ~0ull;
     if (k < n) {
-        for (int j = threadIdx.x; j < n; j += kThreads) keys[j] = a.ss.key(uq0 + j);
+        const KeyGen kg(a.ss);
+        for (int j = threadIdx.x; j < n; j += kThreads) keys[j] = kg.key(uq0 + j);
         __syncthreads();
         auto get = [&](int j) -> unsigned long long {
             return ((unsigned long long)keys[j] << 32) | (unsigned long long)(uq0 + j);
         };
-        T = block_select_kth(get, n, k, hist);
+        // digit: the top 12 bits of the key
+        auto digit = [](unsigned long long c) -> unsigned { return (unsigned)(c >> 52); };
+        auto binmax = [](unsigned b) -> unsigned long long {
+            return ((unsigned long long)b << 52) | ((1ull << 52) - 1ull);
+        };
+        T = block_select_digit(get, n, k, digit, binmax, hist, mem, scan_tmp);
     }
-    int nsel = 0;
-    for (int base = 0; base < n; base += kThreads) {
-        const int j = base + threadIdx.x;
-        bool f = false;
-        if (j < n) f = k == n || ((((unsigned long long)keys[j] << 32) | (uq0 + j)) <= T);
-        int tot;
-        const int off = block_exclusive_scan(f ? 1 : 0, scan_tmp, &tot);
-        if (f) vis[nsel + off] = (uint16_t)j;
-        nsel += tot;
+    // compaction in position order: warp w owns positions [w*seg, (w+1)*seg)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int seg = ((n + kThreads - 1) / kThreads) * 32;
+    const int wb = warp * seg, we = min(n, wb + seg);
+    auto chosen = [&](int j) -> bool {
+        return j < we && (k == n || ((((unsigned long long)keys[j] << 32) | (uq0 + j)) <= T));
+    };
+    int wcnt = 0;
+    for (int j0 = wb; j0 < we; j0 += 32) wcnt += __popc(__ballot_sync(0xffffffffu, chosen(j0 + lane)));
+    if (lane == 0) scan_tmp[warp] = wcnt;
+    __syncthreads();
+    int off = 0, nsel = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+        const int c = scan_tmp[w];
+        off += w < warp ? c : 0;
+        nsel += c;
+    }
+    for (int j0 = wb; j0 < we; j0 += 32) {
+        const bool f = chosen(j0 + lane);
+        const unsigned mk = __ballot_sync(0xffffffffu, f);
+        if (f) vis[off + __popc(mk & ((1u << lane) - 1u))] = (uint16_t)(j0 + lane);
+        off += __popc(mk);
     }
     __syncthreads();
     if (a.mask_out) {
@@ -672,9 +811,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
     gr.init();
     auto getpos = [&](int v) -> uint32_t { return uq0 + vis[v]; };
     gr.run(a, getpos, nsel, uni);
-    gr.reduce(red, sum);
-    build_H<RP>(sum, H, bvec, a.rank, a.lambda);
-    finish_row<RP>(a, row, H, bvec, vsh);
+    gr.reduce(red, a.light_sum + (size_t)blockIdx.x * G::PW);
+}
+
+// Light rows, second kernel: one warp per row builds H = G + lambda I from the
+// row's reduced sums and runs the row update (Alg. 1 lines 8, 10-13), so that
+// the serial power method does not hold a whole block of the reduction kernel.
+template <int RP>
+struct LightFinish {
+    static constexpr int WARPS = RP > 32 ? 4 : 8;
+    static constexpr int PERW = RP * (RP + 1) + 2 * RP;   // floats of H, b and v per warp
+    static constexpr size_t bytes() { return (size_t)WARPS * PERW * 4; }
+};
+
+template <int RP>
+__global__ void __launch_bounds__(LightFinish<RP>::WARPS * 32) k_light_finish(ModeArgs a) {
+    using LF = LightFinish<RP>;
+    constexpr int T = RP / 8, PW = T * (T + 1) / 2 * 64 + RP;
+    extern __shared__ __align__(16) float lf_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * LF::WARPS + warp;
+    if (i >= a.n_light) return;
+    float* H = lf_smem + warp * LF::PERW;
+    float* bvec = H + RP * (RP + 1);
+    float* vsh = bvec + RP;
+    build_H_warp<RP>(a.light_sum + (size_t)i * PW, H, bvec, a.rank, a.lambda, lane);
+    finish_row_warp<RP>(a, a.light_rows[i], H, bvec, vsh, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -696,6 +858,7 @@ __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan
     const int cap = a.chunk_caps[ch].x;
     const longlong2 br = a.heavy_bracket[h];
     const unsigned long long lo = (unsigned long long)br.x, hi = (unsigned long long)br.y;
+    const KeyGen kg(a.ss);
     int nsel = 0, ncand = 0;
     for (uint32_t base = pb; base < pe; base += kThreads * kSamplePer) {
         const uint32_t q0 = base + threadIdx.x * kSamplePer;
@@ -704,7 +867,7 @@ __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan
 #pragma unroll
         for (int j = 0; j < kSamplePer; ++j) {
             const uint32_t q = q0 + j;
-            key[j] = q < pe ? a.ss.key(q) : 0xFFFFFFFFu;
+            key[j] = q < pe ? kg.key(q) : 0xFFFFFFFFu;
             const bool d = q < pe && key[j] < lo;
             const bool cn = q < pe && !d && key[j] < hi;
             nd += d;
@@ -750,7 +913,8 @@ __global__ void __launch_bounds__(kThreads) k_heavy_sample(ModeArgs a) {
 // recomputed keys and its chunk lists are rewritten.
 template <int EW>
 __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
-    __shared__ unsigned hist[256 + 8];
+    __shared__ __align__(16) unsigned hist[kSelBins + 16];
+    __shared__ unsigned long long mem[kSelCap];
     __shared__ int scan_tmp[kThreads / 32 + 1];
     __shared__ int red_i[2][kThreads / 32];
     const int h = blockIdx.x;
@@ -789,24 +953,32 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
         }
         const unsigned long long* cand = a.cand + cbeg;
         auto get = [&](int j) -> unsigned long long { return cand[j]; };
-        // sentinels sort after every real composite, so the m-th smallest over
-        // the whole region is the m-th smallest real candidate
-        const unsigned long long T = block_select_kth(get, ccap, m, hist);
+        // every candidate key lies in the bracket [lo, hi): the digit is the
+        // key's offset in the bracket scaled to 12 bits (sentinels are skipped)
+        const longlong2 br = a.heavy_bracket[h];
+        const unsigned long long lo = (unsigned long long)br.x, w = (unsigned long long)br.y - lo;
+        const int sh = w <= 1ull ? 0 : max(0, 64 - __clzll((long long)(w - 1ull)) - 12);
+        auto digit = [&](unsigned long long c) -> unsigned { return (unsigned)(((c >> 32) - lo) >> sh); };
+        auto binmax = [&](unsigned b) -> unsigned long long {
+            const unsigned long long kmax = lo + (((unsigned long long)b + 1ull) << sh) - 1ull;
+            return kmax >= 0xFFFFFFFFull ? ~0ull : ((kmax << 32) | 0xFFFFFFFFull);
+        };
+        const unsigned long long T = block_select_digit(get, ccap, m, digit, binmax, hist, mem, scan_tmp);
         int ne = 0;
         for (int base = 0; base < ccap; base += kThreads * kSamplePer) {
             const int j0 = base + threadIdx.x * kSamplePer;
+            unsigned long long cv[kSamplePer];
             int nf = 0;
 #pragma unroll
-            for (int u = 0; u < kSamplePer; ++u) nf += (j0 + u < ccap && cand[j0 + u] <= T) ? 1 : 0;
+            for (int u = 0; u < kSamplePer; ++u) {
+                cv[u] = j0 + u < ccap ? cand[j0 + u] : ~0ull;
+                nf += (cv[u] != ~0ull && cv[u] <= T) ? 1 : 0;
+            }
             int tot;
             int off = ne + block_exclusive_scan(nf, scan_tmp, &tot);
 #pragma unroll
-            for (int u = 0; u < kSamplePer; ++u) {
-                if (j0 + u < ccap) {
-                    const unsigned long long cv = cand[j0 + u];
-                    if (cv <= T) a.extra[eoff + off++] = (uint32_t)(cv & 0xFFFFFFFFull);
-                }
-            }
+            for (int u = 0; u < kSamplePer; ++u)
+                if (cv[u] != ~0ull && cv[u] <= T) a.extra[eoff + off++] = (uint32_t)(cv[u] & 0xFFFFFFFFull);
             ne += tot;
         }
         if (threadIdx.x == 0) a.extra_cnt[h] = ne;
@@ -817,8 +989,9 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
     const int64_t q0 = a.row_ptr[row];
     const int n = (int)(a.row_ptr[row + 1] - q0);
     const uint32_t uq0 = (uint32_t)q0;
+    const KeyGen kg(a.ss);
     auto getf = [&](int j) -> unsigned long long {
-        return ((unsigned long long)a.ss.key(uq0 + j) << 32) | (unsigned long long)(uq0 + j);
+        return ((unsigned long long)kg.key(uq0 + j) << 32) | (unsigned long long)(uq0 + j);
     };
     const unsigned long long T = block_select_kth(getf, n, k, hist);
     for (int ch = cb; ch < ce; ++ch) {
@@ -828,7 +1001,7 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
         for (uint32_t base = pb; base < pe; base += kThreads) {
             const uint32_t q = base + threadIdx.x;
             bool f = false;
-            if (q < pe) f = ((((unsigned long long)a.ss.key(q)) << 32) | q) <= T;
+            if (q < pe) f = ((((unsigned long long)kg.key(q)) << 32) | q) <= T;
             int tot;
             const int off = block_exclusive_scan(f ? 1 : 0, scan_tmp, &tot);
             if (f) a.vis[pb + nsel + off] = q;

@@ -64,6 +64,50 @@ struct SampleStream {
     }
 };
 
+// Keys of one sampling stream with the uniform part precomputed.  Within a
+// launch only the counter's last word (the bucket position q) varies, so in
+// rounds 1-3 of Philox4x32-10 one product per round depends on q and the
+// other is the same for every key.  key(q) returns exactly SampleStream::key(q).
+struct KeyGen {
+    uint32_t A, B, D, E, F, k0, k1;
+    __device__ explicit KeyGen(const SampleStream& s) : k0(s.k0), k1(s.k1) {
+        constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+        // round 1 on (mode, iter, inner, .): words 0, 1, 3 are uniform
+        const unsigned long long p0 = (unsigned long long)M0 * s.mode, p1 = (unsigned long long)M1 * s.inner;
+        const uint32_t c0_1 = (uint32_t)(p1 >> 32) ^ s.iter ^ k0, c1_1 = (uint32_t)p1, c3_1 = (uint32_t)p0;
+        A = (uint32_t)(p0 >> 32) ^ k1;            // word 2 after round 1 is A ^ q
+        // round 2: the product of word 0 is uniform
+        B = c1_1 ^ (k0 + W0);
+        const unsigned long long u0 = (unsigned long long)M0 * c0_1;
+        const uint32_t c2_2 = (uint32_t)(u0 >> 32) ^ c3_1 ^ (k1 + W1), c3_2 = (uint32_t)u0;
+        // round 3: the product of word 2 is uniform
+        const unsigned long long u1 = (unsigned long long)M1 * c2_2;
+        D = (uint32_t)(u1 >> 32) ^ (k0 + 2u * W0);
+        F = (uint32_t)u1;
+        E = c3_2 ^ (k1 + 2u * W1);
+    }
+    __device__ __forceinline__ uint32_t key(uint32_t q) const {
+        constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+        const unsigned long long p1 = (unsigned long long)M1 * (A ^ q);
+        const uint32_t c1_2 = (uint32_t)p1;
+        const unsigned long long p0 = (unsigned long long)M0 * ((uint32_t)(p1 >> 32) ^ B);
+        uint32_t c0 = c1_2 ^ D, c1 = F, c2 = (uint32_t)(p0 >> 32) ^ E, c3 = (uint32_t)p0;
+        uint32_t r0 = k0 + 3u * W0, r1 = k1 + 3u * W1;
+#pragma unroll
+        for (int r = 3; r < 10; ++r) {
+            const unsigned long long m0 = (unsigned long long)M0 * c0;
+            const unsigned long long m1 = (unsigned long long)M1 * c2;
+            c0 = (uint32_t)(m1 >> 32) ^ c1 ^ r0;
+            c1 = (uint32_t)m1;
+            c2 = (uint32_t)(m0 >> 32) ^ c3 ^ r1;
+            c3 = (uint32_t)m0;
+            r0 += W0;
+            r1 += W1;
+        }
+        return c0;
+    }
+};
+
 // ---- bfloat16 storage helpers (round to nearest even on store).
 __device__ __forceinline__ float4 bf16x4_to_f32(uint2 v) {
     float4 r;
@@ -154,6 +198,8 @@ struct ModeArgs {
     const int2* heavy_groups; // per heavy row {first group, end group}
     int n_groups;
     float* partial2;          // [n_groups][pw]
+    float* light_sum;         // [n_light][pw] reduced Gram/data sums of light rows
+    int n_light;
     unsigned long long* stat_fallback;  // counter of rows that used the exact selector
     uint8_t* mask_out;        // sampler-only mode: mask over bucket positions
 };
