@@ -61,7 +61,7 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
             ++*L.launches;
         } else {
             e = L.run(NTC_K_HEAVY_GRAM, p.visits_heavy * L.bpv, [&] {
-                k_heavy_gram<RP, EW, BF, NOR><<<p.n_chunks + p.n_heavy, kThreads,
+                k_heavy_gram<RP, EW, BF, NOR><<<p.n_chunks + p.n_heavy, GramNT<RP>::value,
                                            HeavyGramSmem<RP, EW, BF, NOR>::bytes(a.n_other), s>>>(a);
             });
             if (e != cudaSuccess) return e;

@@ -207,7 +207,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // the FMA pass of tile t and the product pass of tile t+1 while the factor
 // rows of tiles t+2, t+3 and the entries of tiles t+4, t+5 are in flight and
 // the bucket positions of tile t+6 are loaded into registers.
-template <int RP, int EW, bool BF16, int NT = kThreads, int NHOT = 0, int NOR = 0, int RREG = 32>
+template <int RP, int EW, bool BF16, int NT = kThreads, int NHOT = 0, int NOR = 0, int RREG = 32, bool PK = false>
 struct Gram {
     static constexpr int T = RP / 8;
     static constexpr int NP = T * (T + 1) / 2;
@@ -252,7 +252,9 @@ struct Gram {
     }
     __host__ __device__ static constexpr size_t total_bytes(int no) { return region_bytes(no) + hot_bytes(no); }
 
-    float acc[8][8];
+    // 8x8 tile; with PK as column pairs for packed FP32 FMA (two round-to-
+    // nearest FMAs per instruction, so the sums equal the scalar form)
+    std::conditional_t<PK, float2[8][4], float[8][8]> acc;
     float4 bq;       // b partial of this thread's product-pass quad
     int g, pa, pb;
     bool active;
@@ -276,7 +278,13 @@ struct Gram {
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            for (int j = 0; j < 8; ++j) {
+                if constexpr (PK) {
+                    if (j < 4) acc[i][j] = make_float2(0.f, 0.f);
+                } else {
+                    acc[i][j] = 0.f;
+                }
+            }
     }
 
     __device__ __forceinline__ static float4 load4(const unsigned char* row, int q) {
@@ -374,11 +382,22 @@ struct Gram {
             const float4 b0 = *reinterpret_cast<const float4*>(kv + 8 * pb);
             const float4 b1 = *reinterpret_cast<const float4*>(kv + 8 * pb + 4);
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            if constexpr (PK) {
+                const float2 bv[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                                      make_float2(b1.z, b1.w)};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 8; ++i) {
+                    const float2 ai = make_float2(av[i], av[i]);
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(av[i], bv[jj], acc[i][jj]);
+                    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = __ffma2_rn(ai, bv[jj], acc[i][jj]);
+                }
+            } else {
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(av[i], bv[jj], acc[i][jj]);
+            }
         }
     }
 
@@ -541,7 +560,12 @@ struct Gram {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) red[(i * 8 + j) * NACT + threadIdx.x] = acc[i][j];
+                for (int j = 0; j < 8; ++j) {
+                    float v;
+                    if constexpr (PK) v = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
+                    else v = acc[i][j];
+                    red[(i * 8 + j) * NACT + threadIdx.x] = v;
+                }
         }
         reinterpret_cast<float4*>(red + NACT * 64)[threadIdx.x] = bq;
         __syncthreads();
@@ -857,36 +881,38 @@ __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan
     const int cand_off = c.w;
     const int cap = a.chunk_caps[ch].x;
     const longlong2 br = a.heavy_bracket[h];
-    const unsigned long long lo = (unsigned long long)br.x, hi = (unsigned long long)br.y;
+    // 32-bit form of key < lo and key < hi (the bounds may equal 2^32)
+    const bool lo_all = br.x > 0xFFFFFFFFll, hi_all = br.y > 0xFFFFFFFFll;
+    const uint32_t lo = lo_all ? 0u : (uint32_t)br.x, hi = hi_all ? 0u : (uint32_t)br.y;
     const KeyGen kg(a.ss);
     int nsel = 0, ncand = 0;
     for (uint32_t base = pb; base < pe; base += kThreads * kSamplePer) {
         const uint32_t q0 = base + threadIdx.x * kSamplePer;
-        uint32_t key[kSamplePer];
-        int nd = 0, nc = 0;
+        // bit j of dm / cm: position q0 + j is certain / a candidate
+        unsigned dm = 0u, cm = 0u;
 #pragma unroll
         for (int j = 0; j < kSamplePer; ++j) {
-            const uint32_t q = q0 + j;
-            key[j] = q < pe ? kg.key(q) : 0xFFFFFFFFu;
-            const bool d = q < pe && key[j] < lo;
-            const bool cn = q < pe && !d && key[j] < hi;
-            nd += d;
-            nc += cn;
+            const uint32_t key = kg.key(q0 + j);
+            const bool in = q0 + j < pe;
+            const bool d = in && (lo_all || key < lo);
+            const bool cn = in && !d && (hi_all || key < hi);
+            dm |= (unsigned)d << j;
+            cm |= (unsigned)cn << j;
         }
         int tot;
-        const int packed = block_exclusive_scan(nd | (nc << 16), scan_tmp, &tot);
+        const int packed = block_exclusive_scan(__popc(dm) | (__popc(cm) << 16), scan_tmp, &tot);
         int od = nsel + (packed & 0xFFFF), oc = ncand + (packed >> 16);
-#pragma unroll
-        for (int j = 0; j < kSamplePer; ++j) {
+        while (dm) {
+            const int j = __ffs(dm) - 1;
+            dm &= dm - 1u;
+            a.vis[pb + od++] = q0 + j;
+        }
+        while (cm) {   // about one position in thirty: the key is recomputed
+            const int j = __ffs(cm) - 1;
+            cm &= cm - 1u;
             const uint32_t q = q0 + j;
-            if (q >= pe) break;
-            const unsigned long long kk = key[j];
-            if (kk < lo) {
-                a.vis[pb + od++] = q;
-            } else if (kk < hi) {
-                if (oc < cap) a.cand[cand_off + oc] = (kk << 32) | q;
-                ++oc;
-            }
+            if (oc < cap) a.cand[cand_off + oc] = ((unsigned long long)kg.key(q) << 32) | q;
+            ++oc;
         }
         nsel += tot & 0xFFFF;
         ncand += tot >> 16;
@@ -1014,7 +1040,17 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
 
 // Heavy rows, step 3: Gram/data partials of each chunk's certain visits and of
 // each row's chosen candidates.
-constexpr int kGramThreads = 256;   // threads per block of the split-row Gram
+// Split-row Gram block shape per padded rank: threads, blocks per SM for the
+// register budget, and packed FP32 FMA.  At R = 32 the packed form needs about
+// 150 registers, so it runs 192 threads at 2 blocks per SM; measured on the
+// Zipf(1.1) 10^4-cube it beats the scalar form at 256 threads (17.4 vs 18.3
+// ms/epoch), while 160 threads at 3 blocks per SM was far slower (28 ms).
+template <int RP>
+struct GramNT {
+    static constexpr bool packed = RP == 32;
+    static constexpr int value = packed ? 192 : 256;
+    static constexpr int blocks = 2;
+};
 // Resident most-frequent rows per other mode in the split-row Gram.  Off:
 // measured on the Zipf(1.1) 10^4-cube, R = 32, the copies it saves cost less
 // than the per-visit selection it adds (28.4 vs 32.5 ms/epoch); the L1-cached
@@ -1026,13 +1062,13 @@ struct HotRows {
 
 template <int RP, int EW, bool BF16, int NOR>
 struct HeavyGramSmem {
-    using G = Gram<RP, EW, BF16, kGramThreads, HotRows<RP>::value, NOR>;
+    using G = Gram<RP, EW, BF16, GramNT<RP>::value, HotRows<RP>::value, NOR, 32, GramNT<RP>::packed>;
     __host__ __device__ static constexpr size_t bytes(int no) { return G::total_bytes(no) + (size_t)G::PW * 4; }
 };
 
 template <int RP, int EW, bool BF16, int NOR>
-__global__ void __launch_bounds__(kGramThreads, 2) k_heavy_gram(ModeArgs a) {
-    using G = Gram<RP, EW, BF16, kGramThreads, HotRows<RP>::value, NOR>;
+__global__ void __launch_bounds__(GramNT<RP>::value, GramNT<RP>::blocks) k_heavy_gram(ModeArgs a) {
+    using G = Gram<RP, EW, BF16, GramNT<RP>::value, HotRows<RP>::value, NOR, 32, GramNT<RP>::packed>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* pipe = smem_raw;
     float* red = reinterpret_cast<float*>(smem_raw);
@@ -1054,7 +1090,7 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_heavy_gram(ModeArgs a) {
     gr.run(a, getpos, cnt, pipe);
     gr.reduce(red, sum);
     float* out = a.partial + (size_t)item * G::PW;
-    for (int s = threadIdx.x; s < G::PW; s += kGramThreads) out[s] = sum[s];
+    for (int s = threadIdx.x; s < G::PW; s += GramNT<RP>::value) out[s] = sum[s];
 }
 
 // Heavy rows, step 4a: a row's items (its chunks in order, then its chosen
