@@ -273,7 +273,7 @@ def run_ntc(args):
     bytes_per_launch = d["alg_bytes"] / max(d["launches"], 1)
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
     kname = {"light": "k_light", "heavy_sample": "k_heavy_sample", "heavy_resolve": "k_heavy_resolve",
-             "heavy_gram": "k_heavy_gram", "heavy_finish": "k_heavy_finish"}[dom]
+             "heavy_gram": "k_heavy_gram", "finish": "k_rows_finish"}[dom]
     total_k = sum(v["ms"] for v in prof.values())
     R, N = p.rank, p.order
     flops_per_visit = (N - 2) * R + 2 * R + R * (R + 1)

@@ -160,11 +160,11 @@ ntc_status ntc_get_stats(ntc_handle* h, ntc_stats* out);
  * visits (index, value and factor-row reads per visit; factor-row traffic per
  * row update), then clears that class.  Errors: NTC_ERR_ARG for a bad kind. */
 enum {
-    NTC_K_LIGHT = 0,          /* fused sample + Gram + row update, one block per row */
-    NTC_K_HEAVY_SAMPLE = 1,   /* keys and certain/candidate split per chunk          */
-    NTC_K_HEAVY_RESOLVE = 2,  /* exact k-subset per split row                        */
-    NTC_K_HEAVY_GRAM = 3,     /* Gram/data partials per chunk                         */
-    NTC_K_HEAVY_FINISH = 4,   /* partial sums and row update per split row           */
+    NTC_K_LIGHT = 0,          /* fused sample + Gram/data sums, one block per row      */
+    NTC_K_HEAVY_SAMPLE = 1,   /* keys and certain/candidate split per chunk            */
+    NTC_K_HEAVY_RESOLVE = 2,  /* exact k-subset per split row                          */
+    NTC_K_HEAVY_GRAM = 3,     /* Gram/data partials per chunk                           */
+    NTC_K_FINISH = 4,         /* split-row partial sums, then every row's update       */
     NTC_K_COUNT = 5
 };
 ntc_status ntc_get_profile(ntc_handle* h, int kind, double* ms, int64_t* launches, int64_t* alg_bytes);

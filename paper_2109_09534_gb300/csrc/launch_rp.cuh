@@ -19,8 +19,7 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         if ((e = set_smem(k_light<RP, EW, BF, NOR>, LightSmem<RP, EW, BF, NOR>::bytes(nomax))) != cudaSuccess) return e;
         if ((e = set_smem(k_heavy_gram<RP, EW, BF, NOR>, HeavyGramSmem<RP, EW, BF, NOR>::bytes(nomax))) != cudaSuccess)
             return e;
-        if ((e = set_smem(k_heavy_finish<RP>, heavy_finish_smem<RP>())) != cudaSuccess) return e;
-        if ((e = set_smem(k_light_finish<RP>, LightFinish<RP>::bytes())) != cudaSuccess) return e;
+        if ((e = set_smem(k_rows_finish<RP>, RowFinish<RP>::bytes())) != cudaSuccess) return e;
         attr = true;
     }
     cudaError_t e = cudaSuccess;
@@ -36,15 +35,10 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     }
     if (p.n_light > 0) {
-        const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv + (int64_t)p.n_light * L.bpr;
+        const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv;
         cudaStream_t ls = fork ? L.h->side : s;
         e = L.run_on(ls, NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
             k_light<RP, EW, BF, NOR><<<p.n_light, kThreads, LightSmem<RP, EW, BF, NOR>::bytes(a.n_other), ls>>>(a);
-            if (!mask_only) {
-                constexpr int W = LightFinish<RP>::WARPS;
-                k_light_finish<RP><<<(p.n_light + W - 1) / W, W * 32, LightFinish<RP>::bytes(), ls>>>(a);
-                ++*L.launches;
-            }
         });
         if (e != cudaSuccess) return e;
         if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;
@@ -65,15 +59,23 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
                                            HeavyGramSmem<RP, EW, BF, NOR>::bytes(a.n_other), s>>>(a);
             });
             if (e != cudaSuccess) return e;
-            e = L.run(NTC_K_HEAVY_FINISH, (int64_t)p.n_heavy * L.bpr, [&] {
+            e = L.run(NTC_K_FINISH, 0, [&] {
                 k_heavy_reduce<RP><<<p.n_groups, kThreads, 0, s>>>(a);
-                k_heavy_finish<RP><<<p.n_heavy, kThreads, heavy_finish_smem<RP>(), s>>>(a);
+                k_heavy_rowsum<RP><<<p.n_heavy, kThreads, 0, s>>>(a);
             });
             ++*L.launches;
             if (e != cudaSuccess) return e;
         }
     }
     if (fork && (e = cudaStreamWaitEvent(s, L.h->ev_join, 0)) != cudaSuccess) return e;
+    const int nrows = p.n_light + p.n_heavy;
+    if (!mask_only && nrows > 0) {
+        constexpr int W = RowFinish<RP>::WARPS;
+        e = L.run(NTC_K_FINISH, (int64_t)nrows * L.bpr, [&] {
+            k_rows_finish<RP><<<(nrows + W - 1) / W, W * 32, RowFinish<RP>::bytes(), s>>>(a);
+        });
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 

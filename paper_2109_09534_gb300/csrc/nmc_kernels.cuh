@@ -236,7 +236,10 @@ struct Gram {
     // RREG registers) one tile ahead instead of through shared memory.
     static constexpr int RS0 = NOR > 0 ? RREG / (NOR * (BF16 ? 2 : 4)) : 1;
     static constexpr int RS = RS0 < 1 ? 1 : (RS0 > 4 ? 4 : RS0);
-    static constexpr int VT = NOR > 0 ? (RS * NT / QPV < NT ? RS * NT / QPV : NT) : VTS;   // visits per tile
+    static constexpr int VTR = RS * NT / QPV < NT ? RS * NT / QPV : NT;   // visits the row slots hold
+    // visits per tile; the packed form takes a whole number of groups so that
+    // no warp runs an extra FMA pass before the tile's barrier
+    static constexpr int VT = NOR > 0 ? (PK && VTR >= NG ? VTR / NG * NG : VTR) : VTS;
     static constexpr int VPG = (VT + NG - 1) / NG;    // visits per group per tile
     static constexpr int PW = NP * 64 + RP;           // reduced floats: the tiles, then b
     static constexpr int RED_BYTES = (NACT * 64 + NT * 4) * 4;
@@ -835,32 +838,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
     gr.init();
     auto getpos = [&](int v) -> uint32_t { return uq0 + vis[v]; };
     gr.run(a, getpos, nsel, uni);
-    gr.reduce(red, a.light_sum + (size_t)blockIdx.x * G::PW);
+    gr.reduce(red, a.row_sum + (size_t)blockIdx.x * G::PW);
 }
 
-// Light rows, second kernel: one warp per row builds H = G + lambda I from the
-// row's reduced sums and runs the row update (Alg. 1 lines 8, 10-13), so that
-// the serial power method does not hold a whole block of the reduction kernel.
+// Row update of every sampled row (Alg. 1 lines 8, 10-13): one warp per row
+// builds H = G + lambda I from the row's reduced sums -- light rows first,
+// then split rows -- and runs the power method and the projected momentum
+// step, so that the serial part does not hold a whole block.
 template <int RP>
-struct LightFinish {
+struct RowFinish {
     static constexpr int WARPS = RP > 32 ? 4 : 8;
     static constexpr int PERW = RP * (RP + 1) + 2 * RP;   // floats of H, b and v per warp
     static constexpr size_t bytes() { return (size_t)WARPS * PERW * 4; }
 };
 
 template <int RP>
-__global__ void __launch_bounds__(LightFinish<RP>::WARPS * 32) k_light_finish(ModeArgs a) {
-    using LF = LightFinish<RP>;
+__global__ void __launch_bounds__(RowFinish<RP>::WARPS * 32) k_rows_finish(ModeArgs a) {
+    using RF = RowFinish<RP>;
     constexpr int T = RP / 8, PW = T * (T + 1) / 2 * 64 + RP;
-    extern __shared__ __align__(16) float lf_smem[];
+    extern __shared__ __align__(16) float rf_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * LF::WARPS + warp;
-    if (i >= a.n_light) return;
-    float* H = lf_smem + warp * LF::PERW;
+    const int i = blockIdx.x * RF::WARPS + warp;
+    if (i >= a.n_light + a.n_heavy) return;
+    const int row = i < a.n_light ? a.light_rows[i] : a.heavy[i - a.n_light].x;
+    float* H = rf_smem + warp * RF::PERW;
     float* bvec = H + RP * (RP + 1);
     float* vsh = bvec + RP;
-    build_H_warp<RP>(a.light_sum + (size_t)i * PW, H, bvec, a.rank, a.lambda, lane);
-    finish_row_warp<RP>(a, a.light_rows[i], H, bvec, vsh, lane);
+    build_H_warp<RP>(a.row_sum + (size_t)i * PW, H, bvec, a.rank, a.lambda, lane);
+    finish_row_warp<RP>(a, row, H, bvec, vsh, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1120,19 +1125,14 @@ __global__ void __launch_bounds__(kThreads) k_heavy_reduce(ModeArgs a) {
     }
 }
 
-// Heavy rows, step 4b: fixed-order sum of the row's group sums, then the row
-// update.
+// Heavy rows, step 4b: fixed-order sum of the row's group sums into the row's
+// slot of the reduced-sum buffer (the update itself is k_rows_finish).
 template <int RP>
-__global__ void __launch_bounds__(kThreads) k_heavy_finish(ModeArgs a) {
+__global__ void __launch_bounds__(kThreads) k_heavy_rowsum(ModeArgs a) {
     constexpr int T = RP / 8, NP = T * (T + 1) / 2, PW = NP * 64 + RP;
-    extern __shared__ __align__(16) float smem[];
-    float* sum = smem;
-    float* H = sum + PW;
-    float* bvec = H + RP * (RP + 1);
-    float* vsh = bvec + RP;
     const int h = blockIdx.x;
-    const int4 hv = a.heavy[h];
     const int2 gg = a.heavy_groups[h];   // {first group, end group}
+    float* out = a.row_sum + (size_t)(a.n_light + h) * PW;
     for (int s = threadIdx.x; s < PW; s += kThreads) {
         float t = 0.f;
         int g = gg.x;
@@ -1144,11 +1144,8 @@ __global__ void __launch_bounds__(kThreads) k_heavy_finish(ModeArgs a) {
             for (int u = 0; u < 8; ++u) t += v[u];
         }
         for (; g < gg.y; ++g) t += a.partial2[(size_t)g * PW + s];
-        sum[s] = t;
+        out[s] = t;
     }
-    __syncthreads();
-    build_H<RP>(sum, H, bvec, a.rank, a.lambda);
-    finish_row<RP>(a, hv.x, H, bvec, vsh);
 }
 
 // Sampler-only mode for heavy rows: mark the chosen positions.
@@ -1168,9 +1165,5 @@ __global__ void k_heavy_mask(ModeArgs a) {
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) a.mask_out[list[i]] = 1;
 }
 
-template <int RP>
-constexpr size_t heavy_finish_smem() {
-    return (size_t)((RP / 8) * (RP / 8 + 1) / 2 * 64 + RP + RP * (RP + 1) + 2 * RP + 8) * 4;
-}
 
 }  // namespace ntc

@@ -180,7 +180,8 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     NTC_CUDA(h, h->partial.ensure(sizeof(float) * (size_t)partial_width(h->rp) *
                                   (size_t)std::max(p.n_chunks + p.n_heavy, 1)));
     NTC_CUDA(h, h->partial2.ensure(sizeof(float) * (size_t)partial_width(h->rp) * (size_t)std::max(p.n_groups, 1)));
-    NTC_CUDA(h, h->light_sum.ensure(sizeof(float) * (size_t)partial_width(h->rp) * (size_t)std::max(p.n_light, 1)));
+    NTC_CUDA(h, h->row_sum.ensure(sizeof(float) * (size_t)partial_width(h->rp) *
+                                  (size_t)std::max(p.n_light + p.n_heavy, 1)));
     p.valid = true;
     return NTC_OK;
 }
@@ -238,7 +239,7 @@ ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t a
     a.heavy_groups = p.heavy_groups.as<int2>();
     a.n_groups = p.n_groups;
     a.partial2 = h->partial2.as<float>();
-    a.light_sum = h->light_sum.as<float>();
+    a.row_sum = h->row_sum.as<float>();
     a.n_light = p.n_light;
     a.stat_fallback = h->stat.as<unsigned long long>();
     a.mask_out = nullptr;

@@ -93,7 +93,7 @@ struct ntc_handle {
     std::vector<int64_t> row_ptr_h[ntc::kMaxOrder];
     ntc::ModePlan plan[ntc::kMaxOrder];
     // scratch
-    ntc::DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, partial2, light_sum, stat, red,
+    ntc::DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, partial2, row_sum, stat, red,
         mask;
     // per-kernel event timing ("profile")
     int profile = 0;

@@ -198,7 +198,7 @@ struct ModeArgs {
     const int2* heavy_groups; // per heavy row {first group, end group}
     int n_groups;
     float* partial2;          // [n_groups][pw]
-    float* light_sum;         // [n_light][pw] reduced Gram/data sums of light rows
+    float* row_sum;           // [n_light + n_heavy][pw] reduced Gram/data sums: light rows, then split rows
     int n_light;
     unsigned long long* stat_fallback;  // counter of rows that used the exact selector
     uint8_t* mask_out;        // sampler-only mode: mask over bucket positions

@@ -21,7 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ntc.h")
 
 NTC_OK, NTC_ERR_ARG, NTC_ERR_INDEX, NTC_ERR_OOM, NTC_ERR_STATE, NTC_ERR_CUDA = range(6)
-KERNELS = ["light", "heavy_sample", "heavy_resolve", "heavy_gram", "heavy_finish"]
+KERNELS = ["light", "heavy_sample", "heavy_resolve", "heavy_gram", "finish"]
 _STATUS = {0: "NTC_OK", 1: "NTC_ERR_ARG", 2: "NTC_ERR_INDEX", 3: "NTC_ERR_OOM", 4: "NTC_ERR_STATE",
            5: "NTC_ERR_CUDA"}
 
