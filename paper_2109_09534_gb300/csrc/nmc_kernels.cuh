@@ -242,7 +242,10 @@ struct Gram {
     static constexpr int VT = NOR > 0 ? (PK && VTR >= NG ? VTR / NG * NG : VTR) : VTS;
     static constexpr int VPG = (VT + NG - 1) / NG;    // visits per group per tile
     static constexpr int PW = NP * 64 + RP;           // reduced floats: the tiles, then b
-    static constexpr int RED_BYTES = (NACT * 64 + NT * 4) * 4;
+    // slot stride of the reduction buffer: odd, so that the column reads of
+    // consecutive slots fall in distinct banks
+    static constexpr int RSTR = NACT | 1;
+    static constexpr int RED_BYTES = (RSTR * 64 + NT * 4) * 4;
     static_assert(NT % QPV == 0, "a thread's product-pass quad must be fixed");
 
     __host__ __device__ static constexpr size_t pipe_bytes(int no) {
@@ -556,7 +559,7 @@ struct Gram {
 
     // Fixed-order reduction over the NG groups (tiles) and over the threads of
     // each product quad (b) into sum[PW] (shared); `red` may alias `pipe`.
-    // The buffer is slot-major (red[slot * NACT + thread]) so that a warp's
+    // The buffer is slot-major (red[slot * RSTR + thread]) so that a warp's
     // stores fall in consecutive banks.
     __device__ __forceinline__ void reduce(float* red, float* sum) {
         if (active) {
@@ -567,14 +570,14 @@ struct Gram {
                     float v;
                     if constexpr (PK) v = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
                     else v = acc[i][j];
-                    red[(i * 8 + j) * NACT + threadIdx.x] = v;
+                    red[(i * 8 + j) * RSTR + threadIdx.x] = v;
                 }
         }
-        reinterpret_cast<float4*>(red + NACT * 64)[threadIdx.x] = bq;
+        reinterpret_cast<float4*>(red + RSTR * 64)[threadIdx.x] = bq;   // 16-byte aligned: RSTR * 64 % 4 == 0
         __syncthreads();
         for (int s = threadIdx.x; s < NP * 64; s += NT) {
             const int p = s >> 6, ij = s & 63;
-            const float* col = red + ij * NACT + p;
+            const float* col = red + ij * RSTR + p;
             float t = 0.f;
             for (int gg = 0; gg < NG; ++gg) t += col[gg * NP];
             sum[s] = t;
@@ -582,7 +585,7 @@ struct Gram {
         for (int r = threadIdx.x; r < RP; r += NT) {
             const int q = r / 4, c = r % 4;
             float t = 0.f;
-            for (int th = q; th < NT; th += QPV) t += red[NACT * 64 + th * 4 + c];
+            for (int th = q; th < NT; th += QPV) t += red[RSTR * 64 + th * 4 + c];
             sum[NP * 64 + r] = t;
         }
         __syncthreads();
@@ -1047,14 +1050,15 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
 // each row's chosen candidates.
 // Split-row Gram block shape per padded rank: threads, blocks per SM for the
 // register budget, and packed FP32 FMA.  At R = 32 the packed form needs about
-// 150 registers, so it runs 192 threads at 2 blocks per SM; measured on the
-// Zipf(1.1) 10^4-cube it beats the scalar form at 256 threads (17.4 vs 18.3
-// ms/epoch), while 160 threads at 3 blocks per SM was far slower (28 ms).
+// 150 registers; measured on the Zipf(1.1) 10^4-cube (ms/epoch of this
+// kernel): packed 128 threads x 3 blocks 16.3, packed 192 x 2 17.1, scalar
+// 256 x 2 18.0, scalar 160 x 3 18.4, scalar 128 x 4 19.2.
 template <int RP>
 struct GramNT {
     static constexpr bool packed = RP == 32;
-    static constexpr int value = packed ? 192 : 256;
-    static constexpr int blocks = 2;
+    static constexpr int value = packed ? 128 : 256;
+    static constexpr int blocks = packed ? 3 : 2;
+    static constexpr int rreg = 32;   // registers for factor rows loaded one tile ahead
 };
 // Resident most-frequent rows per other mode in the split-row Gram.  Off:
 // measured on the Zipf(1.1) 10^4-cube, R = 32, the copies it saves cost less
@@ -1067,13 +1071,13 @@ struct HotRows {
 
 template <int RP, int EW, bool BF16, int NOR>
 struct HeavyGramSmem {
-    using G = Gram<RP, EW, BF16, GramNT<RP>::value, HotRows<RP>::value, NOR, 32, GramNT<RP>::packed>;
+    using G = Gram<RP, EW, BF16, GramNT<RP>::value, HotRows<RP>::value, NOR, GramNT<RP>::rreg, GramNT<RP>::packed>;
     __host__ __device__ static constexpr size_t bytes(int no) { return G::total_bytes(no) + (size_t)G::PW * 4; }
 };
 
 template <int RP, int EW, bool BF16, int NOR>
 __global__ void __launch_bounds__(GramNT<RP>::value, GramNT<RP>::blocks) k_heavy_gram(ModeArgs a) {
-    using G = Gram<RP, EW, BF16, GramNT<RP>::value, HotRows<RP>::value, NOR, 32, GramNT<RP>::packed>;
+    using G = Gram<RP, EW, BF16, GramNT<RP>::value, HotRows<RP>::value, NOR, GramNT<RP>::rreg, GramNT<RP>::packed>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* pipe = smem_raw;
     float* red = reinterpret_cast<float*>(smem_raw);
