@@ -235,7 +235,8 @@ struct Gram {
     // to registers (RS product slots of four elements per row per thread, about
     // RREG registers) one tile ahead instead of through shared memory.
     static constexpr int RS0 = NOR > 0 ? RREG / (NOR * (BF16 ? 2 : 4)) : 1;
-    static constexpr int RS = RS0 < 1 ? 1 : (RS0 > 4 ? 4 : RS0);
+    static constexpr int RSMAX = PK ? 8 : 4;
+    static constexpr int RS = RS0 < 1 ? 1 : (RS0 > RSMAX ? RSMAX : RS0);
     static constexpr int VTR = RS * NT / QPV < NT ? RS * NT / QPV : NT;   // visits the row slots hold
     // visits per tile; the packed form takes a whole number of groups so that
     // no warp runs an extra FMA pass before the tile's barrier
@@ -1052,13 +1053,15 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
 // register budget, and packed FP32 FMA.  At R = 32 the packed form needs about
 // 150 registers; measured on the Zipf(1.1) 10^4-cube (ms/epoch of this
 // kernel): packed 128 threads x 3 blocks 16.3, packed 192 x 2 17.1, scalar
-// 256 x 2 18.0, scalar 160 x 3 18.4, scalar 128 x 4 19.2.
+// 256 x 2 18.0, scalar 160 x 3 18.4, scalar 128 x 4 19.2.  Deeper row
+// prefetch pays: 5 row slots per thread (40 registers, 154 in all) 15.7,
+// 6 slots 16.1, 2 slots with 4 blocks per SM 22.7.
 template <int RP>
 struct GramNT {
     static constexpr bool packed = RP == 32;
     static constexpr int value = packed ? 128 : 256;
     static constexpr int blocks = packed ? 3 : 2;
-    static constexpr int rreg = 32;   // registers for factor rows loaded one tile ahead
+    static constexpr int rreg = packed ? 40 : 32;   // registers for factor rows loaded one tile ahead
 };
 // Resident most-frequent rows per other mode in the split-row Gram.  Off:
 // measured on the Zipf(1.1) 10^4-cube, R = 32, the copies it saves cost less
