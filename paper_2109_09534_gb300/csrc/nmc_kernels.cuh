@@ -607,33 +607,6 @@ __device__ __forceinline__ void pair_ab(int T, int p, int* a, int* b) {
     *b = 0;
 }
 
-// Expand the reduced tiles into H = G + lambda I (full symmetric, stride RP+1)
-// and b (Alg. 1 lines 6 and 9).
-template <int RP>
-__device__ __forceinline__ void build_H(const float* sum, float* H, float* bvec, int R, float lambda) {
-    constexpr int T = RP / 8, NP = T * (T + 1) / 2;
-    for (int s = threadIdx.x; s < NP * 64; s += kThreads) {
-        const int p = s >> 6, ij = s & 63, i = ij >> 3, j = ij & 7;
-        int a, b;
-        pair_ab(T, p, &a, &b);
-        const int r = 8 * a + i, c = 8 * b + j;
-        if (a == b && i > j) continue;
-        const float v = sum[p * 64 + ij];
-        H[r * (RP + 1) + c] = v;
-        H[c * (RP + 1) + r] = v;
-    }
-    for (int r = threadIdx.x; r < RP; r += kThreads) bvec[r] = sum[NP * 64 + r];
-    __syncthreads();
-    if (threadIdx.x < R) H[threadIdx.x * (RP + 1) + threadIdx.x] += lambda;
-    __syncthreads();
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // Alg. 1 lines 8 and 10-13 for row p, run by warp 0: gradient H y - b
 // (= W + Z + lambda y), L_p by the power method (v0 = ones/sqrt(R), fixed
 // iteration count, Rayleigh quotient), projected step, momentum, extrapolation.
@@ -653,17 +626,37 @@ __device__ __forceinline__ void finish_row_warp(const ModeArgs& a, int p, const 
         y[t] = in ? (a.read_y ? a.Y[base + r] : al[t]) : 0.f;
         v[t] = in ? 1.0f / sqrtf((float)R) : 0.f;
     }
+    // for RP <= 32 lane r keeps row r of H in registers; x is read as float4
+    // broadcasts (the sums run over c in the same order either way)
+    float hrow[RP <= 32 ? RP : 1];
+    if constexpr (RP <= 32) {
+#pragma unroll
+        for (int c = 0; c < RP; ++c) hrow[c] = lane < RP ? H[lane * (RP + 1) + c] : 0.f;
+    }
     auto matvec = [&](const float* x, float* out) {
-#pragma unroll
-        for (int t = 0; t < PER; ++t) {
-            const int r = lane + 32 * t;
+        if constexpr (RP <= 32) {
             float s = 0.f;
-            if (r < RP) {
-                const float* hr = H + r * (RP + 1);
 #pragma unroll
-                for (int c = 0; c < RP; ++c) s = fmaf(hr[c], x[c], s);
+            for (int c = 0; c < RP; c += 4) {
+                const float4 x4 = *reinterpret_cast<const float4*>(x + c);
+                s = fmaf(hrow[c], x4.x, s);
+                s = fmaf(hrow[c + 1], x4.y, s);
+                s = fmaf(hrow[c + 2], x4.z, s);
+                s = fmaf(hrow[c + 3], x4.w, s);
             }
-            out[t] = s;
+            out[0] = s;
+        } else {
+#pragma unroll
+            for (int t = 0; t < PER; ++t) {
+                const int r = lane + 32 * t;
+                float s = 0.f;
+                if (r < RP) {
+                    const float* hr = H + r * (RP + 1);
+#pragma unroll
+                    for (int c = 0; c < RP; ++c) s = fmaf(hr[c], x[c], s);
+                }
+                out[t] = s;
+            }
         }
     };
     // gradient: (H y)_r - b_r
@@ -727,29 +720,33 @@ __device__ __forceinline__ void finish_row_warp(const ModeArgs& a, int p, const 
     }
 }
 
-template <int RP>
-__device__ __forceinline__ void finish_row(const ModeArgs& a, int p, const float* H, const float* bvec,
-                                           float* vsh) {
-    if (threadIdx.x < 32) finish_row_warp<RP>(a, p, H, bvec, vsh, threadIdx.x);
-}
-
-// build_H for one warp: the reduced tiles of one row (global memory) into the
-// warp's own H (stride RP+1) and b.
+// H = G + lambda I for one row, built by one warp: the reduced tiles of the
+// row (global memory) into the warp's own H (full symmetric, stride RP+1) and b.
 template <int RP>
 __device__ __forceinline__ void build_H_warp(const float* sum, float* H, float* bvec, int R, float lambda,
                                              int lane) {
-    constexpr int T = RP / 8, NP = T * (T + 1) / 2;
-    for (int s = lane; s < NP * 64; s += 32) {
+    constexpr int T = RP / 8, NP = T * (T + 1) / 2, NS = NP * 64 / 32;
+    // every load of the row's sums is issued before the first store
+    float v[NS];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) v[u] = sum[u * 32 + lane];
+    float bv[(RP + 31) / 32];
+#pragma unroll
+    for (int u = 0; u < (RP + 31) / 32; ++u) bv[u] = u * 32 + lane < RP ? sum[NP * 64 + u * 32 + lane] : 0.f;
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+        const int s = u * 32 + lane;
         const int p = s >> 6, ij = s & 63, i = ij >> 3, j = ij & 7;
         int a, b;
         pair_ab(T, p, &a, &b);
         const int r = 8 * a + i, c = 8 * b + j;
         if (a == b && i > j) continue;
-        const float v = sum[p * 64 + ij];
-        H[r * (RP + 1) + c] = v;
-        H[c * (RP + 1) + r] = v;
+        H[r * (RP + 1) + c] = v[u];
+        H[c * (RP + 1) + r] = v[u];
     }
-    for (int r = lane; r < RP; r += 32) bvec[r] = sum[NP * 64 + r];
+#pragma unroll
+    for (int u = 0; u < (RP + 31) / 32; ++u)
+        if (u * 32 + lane < RP) bvec[u * 32 + lane] = bv[u];
     __syncwarp();
     for (int r = lane; r < R; r += 32) H[r * (RP + 1) + r] += lambda;
     __syncwarp();
@@ -1116,7 +1113,9 @@ __global__ void __launch_bounds__(kThreads) k_heavy_reduce(ModeArgs a) {
     const int h = gr.x;
     const int4 hv = a.heavy[h];
     const int nitems = hv.w - hv.z + 1;
-    float* out = a.partial2 + (size_t)blockIdx.x * PW;
+    // a row with a single group has its final sum here
+    const int2 gg = a.heavy_groups[h];
+    float* out = gg.y - gg.x == 1 ? a.row_sum + (size_t)(a.n_light + h) * PW : a.partial2 + (size_t)blockIdx.x * PW;
     for (int s = threadIdx.x; s < PW; s += kThreads) {
         float v[kReduceGroup];
 #pragma unroll
@@ -1139,6 +1138,7 @@ __global__ void __launch_bounds__(kThreads) k_heavy_rowsum(ModeArgs a) {
     constexpr int T = RP / 8, NP = T * (T + 1) / 2, PW = NP * 64 + RP;
     const int h = blockIdx.x;
     const int2 gg = a.heavy_groups[h];   // {first group, end group}
+    if (gg.y - gg.x == 1) return;        // written by k_heavy_reduce
     float* out = a.row_sum + (size_t)(a.n_light + h) * PW;
     for (int s = threadIdx.x; s < PW; s += kThreads) {
         float t = 0.f;
