@@ -41,6 +41,17 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage-bf16", action="store_true")
+    # serving stream (continuous-batching completion server)
+    ap.add_argument("--serve", action="store_true", help="run the serving stream instead of the epoch bench")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="full stream: 256 jobs, mode sizes 1e3..2e5, 1M..50M observations")
+    ap.add_argument("--serve-jobs", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="mean job arrivals per second")
+    ap.add_argument("--serve-dims", default="1000,20000", help="log-uniform mode-size range")
+    ap.add_argument("--serve-nnz", default="1000000,5000000", help="log-uniform observation range")
+    ap.add_argument("--serve-budget", type=float, default=150e9, help="HBM budget, bytes")
+    ap.add_argument("--serve-max-epochs", type=int, default=40)
+    ap.add_argument("--serve-qps", type=float, default=10000.0, help="prediction queries per second")
     return ap.parse_args()
 
 
@@ -69,10 +80,16 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# sources of the epoch kernels (the serving runtime and the host API are not
+# part of what the DRAM counters measured)
+KERNEL_SOURCES = ("ntc_internal.cuh", "nmc_kernels.cuh", "launch_rp.cuh",
+                  "nmc_rp8.cu", "nmc_rp16.cu", "nmc_rp32.cu", "nmc_rp64.cu")
+
+
 def csrc_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2109_09534_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -329,8 +346,95 @@ def run_ntc(args):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving stream: Poisson job arrivals admitted under the HBM budget, each
+    job run epoch by epoch until its held-out RMSE reaches 1.1 sigma (or the
+    epoch limit), with Poisson prediction queries against running jobs
+    batched into one multi-job launch per tick."""
+    import numpy as np
+    import torch
+
+    from paper_2109_09534_gb300 import ntc, synth
+
+    torch.cuda.set_device(0)
+    if args.serve_full:
+        args.serve_jobs, args.serve_dims, args.serve_nnz = 256, "1000,200000", "1000000,50000000"
+    dlo, dhi = (float(x) for x in args.serve_dims.split(","))
+    nlo, nhi = (float(x) for x in args.serve_nnz.split(","))
+    specs = synth.serving_stream(args.serve_jobs, rate=args.serve_rate, dim_range=(dlo, dhi),
+                                 nnz_range=(nlo, nhi))
+    sigma = 0.01
+    target = 1.1 * sigma
+    t_gen = time.perf_counter()
+    probs = [synth.serving_job(s, sigma=sigma, test_frac=0.01) for s in specs]
+    t_gen = time.perf_counter() - t_gen
+    srv = ntc.Server(args.serve_budget, 64)
+    clocks = Clocks(0)
+    clocks.start()
+    t0 = srv.now()
+    ids = []
+    for k, (s, p) in enumerate(zip(specs, probs)):
+        ids.append(srv.submit(p.dims, p.rank, p.lam, p.c, p.idx_train, p.val_train, p.idx_test, p.val_test,
+                              target, args.serve_max_epochs, arrival=t0 + s.arrival, seed=1000 + 97 * k,
+                              init_seed=3, storage_bf16=s.storage_bf16))
+    rng = np.random.default_rng(7)
+    lat = []
+    t_q = srv.now()
+    pending = []          # arrival times of queries not yet served
+    while True:
+        srv.step()
+        now = srv.now()
+        # queries that arrived since the last tick (Poisson), against running jobs
+        nq = rng.poisson(args.serve_qps * (now - t_q))
+        pending += list(np.sort(rng.uniform(t_q, now, nq)))
+        t_q = now
+        running = [(j, probs[j]) for j in ids if srv.job_info(j)["state"] == ntc.JOB_RUNNING]
+        if pending and running:
+            pick = rng.integers(0, len(running), len(pending))
+            q_job = np.array([j for j, _ in running], dtype=np.int64)[pick]
+            dmat = np.ones((len(running), 8))
+            for r, (_, p) in enumerate(running):
+                dmat[r, :len(p.dims)] = p.dims
+            q_idx = (rng.random((len(pending), 8)) * dmat[pick]).astype(np.int32)   # padding columns stay 0
+            srv.predict(q_job, q_idx)
+            t_ret = srv.now()
+            lat += [t_ret - a for a in pending]
+            pending = []
+        if all(srv.job_info(j)["state"] >= ntc.JOB_DONE for j in ids):
+            break
+        time.sleep(0.0002)
+    wall = srv.now() - t0
+    clk = clocks.stop()
+    infos = [srv.job_info(j) for j in ids]
+    st = srv.stats()
+    reached = [i for i in infos if i["reached"]]
+    ttt = np.array([i["t_done"] - i["t_arrival"] for i in reached]) if reached else np.array([np.nan])
+    lat_ms = np.array(lat) * 1e3 if lat else np.array([np.nan])
+    line = {"metric": "serving p50/p99 time-to-target-RMSE", "unit": "s", "mode": "serve",
+            "value": float(np.percentile(ttt, 50)), "p50_time_to_target_s": float(np.percentile(ttt, 50)),
+            "p99_time_to_target_s": float(np.percentile(ttt, 99)), "higher_is_better": False,
+            "jobs": len(ids), "reached": len(reached), "failed": st["failed"],
+            "censored_at_max_epochs": sum(1 for i in infos if i["state"] == ntc.JOB_DONE and not i["reached"]),
+            "query_latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                                 "queries": st["predict_queries"], "launches": st["predict_launches"]},
+            "entries_per_s": st["entries"] / wall, "epochs": st["epochs"], "wall_s": wall,
+            "peak_running": st["peak_running"], "peak_bytes": st["peak_bytes"], "budget_bytes": args.serve_budget,
+            "n_gpus": 1, "data": "synthetic", "dtype": "f32 / bf16-storage (half the jobs each)", "clocks": clk,
+            "config": {"workload": f"{args.serve_jobs} jobs, Poisson {args.serve_rate}/s, order 3-4, mode sizes "
+                                   f"log-uniform {args.serve_dims}, R in 8/16/32/64, observations log-uniform "
+                                   f"{args.serve_nnz}, uniform indices, planted U[0,1], sigma 0.01, target "
+                                   f"RMSE 1.1 sigma, max {args.serve_max_epochs} epochs, "
+                                   f"{args.serve_qps:.0f} queries/s",
+                       "generation_s": t_gen}}
+    srv.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.serve:
+        run_serve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

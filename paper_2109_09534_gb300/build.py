@@ -26,7 +26,7 @@ def sources():
 
 def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        [os.path.join(ROOT, "include", "ntc.h")]
+        glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
 def _stale() -> bool:

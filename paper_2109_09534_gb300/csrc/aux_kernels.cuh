@@ -281,6 +281,14 @@ __global__ void k_predict(FactorSet f, const int32_t* idx, int64_t n, float* out
         out[e] = model_at(f, idx + e * f.order);
 }
 
+// Queries of several jobs in one launch: query e reads job table[slot[e]] at
+// the index idx[e * kMaxOrder ...] (entries past that job's order unused).
+__global__ void k_predict_multi(const FactorSet* table, const int32_t* slot, const int32_t* idx, int64_t n,
+                                float* out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = model_at(table[slot[e]], idx + e * kMaxOrder);
+}
+
 // Per-block double sums of (x - model)^2.
 __global__ void __launch_bounds__(kThreads) k_sq_resid(FactorSet f, const int32_t* idx, const float* vals,
                                                        int64_t n, double* partial) {

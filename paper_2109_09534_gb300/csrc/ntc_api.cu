@@ -502,6 +502,51 @@ FactorSet factor_set(ntc_handle* h) {
 
 }  // namespace
 
+// ---- serving-runtime entry points (declared in ntc_host.h) ---------------------
+namespace ntc {
+
+cudaError_t rmse_enqueue(ntc_handle* h, const int32_t* idx, const float* vals, int64_t n, double* scratch,
+                         double* host_sum) {
+    const int gb = grid_for(n, 256, kRmseScratch - 1);
+    k_sq_resid<<<gb, kThreads, 0, h->stream>>>(factor_set(h), idx, vals, n, scratch);
+    k_sum_partials<<<1, kThreads, 0, h->stream>>>(scratch, gb, scratch + (kRmseScratch - 1));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(host_sum, scratch + (kRmseScratch - 1), sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream);
+}
+
+size_t factor_table_bytes() { return sizeof(FactorSet); }
+
+cudaError_t predict_multi(ntc_handle* const* handles, int nh, const int32_t* slot, const int32_t* idx, int64_t n,
+                          float* out, void* table, cudaStream_t s) {
+    std::vector<FactorSet> t((size_t)nh);
+    for (int j = 0; j < nh; ++j) t[(size_t)j] = factor_set(handles[j]);
+    // pageable source: the copy is staged before the call returns
+    cudaError_t e = cudaMemcpyAsync(table, t.data(), sizeof(FactorSet) * (size_t)nh, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess || n == 0) return e;
+    k_predict_multi<<<grid_for(n), 256, 0, s>>>(static_cast<const FactorSet*>(table), slot, idx, n, out);
+    return cudaGetLastError();
+}
+
+int64_t handle_device_bytes(const ntc_handle* h) {
+    int64_t b = 0;
+    for (int i = 0; i < kMaxOrder; ++i) {
+        b += (int64_t)(h->U[i].bytes + h->Ub[i].bytes + h->row_ptr[i].bytes + h->bucket[i].bytes + h->perm[i].bytes +
+                       h->inv_dev[i].bytes + h->rows_dev[i].bytes);
+        const ModePlan& p = h->plan[i];
+        b += (int64_t)(p.light_rows.bytes + p.light_k.bytes + p.chunks.bytes + p.chunk_caps.bytes + p.heavy.bytes +
+                       p.bracket.bytes + p.heavy_cand.bytes + p.groups.bytes + p.heavy_groups.bytes);
+    }
+    b += (int64_t)(h->Y.bytes + h->coo_idx.bytes + h->coo_val.bytes + h->dims_dev.bytes + h->vis.bytes +
+                   h->vis_cnt.bytes + h->cand.bytes + h->cand_cnt.bytes + h->extra.bytes + h->extra_cnt.bytes +
+                   h->flags.bytes + h->partial.bytes + h->partial2.bytes + h->row_sum.bytes + h->stat.bytes +
+                   h->red.bytes + h->mask.bytes);
+    return b;
+}
+
+}  // namespace ntc
+
 // ---- allocation-free RMSE -----------------------------------------------------
 // One double of partial sum per block of kNoAllocPerBlock queries, plus the
 // final sum, in a file-scope device array: every GPU that loads the library

@@ -161,4 +161,20 @@ extern template cudaError_t launch_mode_rp<16>(int, bool, const ModeArgs&, const
 extern template cudaError_t launch_mode_rp<32>(int, bool, const ModeArgs&, const ModePlan&, Launcher&, bool);
 extern template cudaError_t launch_mode_rp<64>(int, bool, const ModeArgs&, const ModePlan&, Launcher&, bool);
 
+// ---- entry points for the serving runtime (serve.cu), in ntc_api.cu ---------
+// Held-out squared residual sum of the handle's current factors, reduced on
+// the handle's stream into scratch (>= kRmseScratch doubles, device) and copied
+// to *host_sum (pinned host memory) -- nothing waits.
+constexpr int kRmseScratch = 1025;
+cudaError_t rmse_enqueue(ntc_handle* h, const int32_t* idx, const float* vals, int64_t n, double* scratch,
+                         double* host_sum);
+// CP model values for n queries over several handles in one kernel launch on
+// stream s: query e uses handles[slot[e]] and idx[e * kMaxOrder ...]; table
+// is device memory for nh factor tables (>= nh * factor_table_bytes()).
+size_t factor_table_bytes();
+cudaError_t predict_multi(ntc_handle* const* handles, int nh, const int32_t* slot, const int32_t* idx, int64_t n,
+                          float* out, void* table, cudaStream_t s);
+// Device bytes the handle holds now.
+int64_t handle_device_bytes(const ntc_handle* h);
+
 }  // namespace ntc

@@ -1,0 +1,423 @@
+// serve.cu -- the continuous-batching completion server of include/ntc_serve.h.
+//
+// Each admitted job owns an ntc_handle (its bucketed observations, factors
+// and scratch stay on the device) and a non-blocking CUDA stream.  A tick
+// collects finished epochs, admits queued jobs under the HBM budget, and
+// enqueues one epoch plus a device RMSE reduction for every idle job; the
+// epochs of different jobs then run concurrently on the GPU.  Prediction
+// queries over many jobs go to one multi-job kernel launch.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <deque>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ntc_serve.h"
+#include "ntc_host.h"
+
+namespace {
+
+using ntc::DevMem;
+
+struct Job {
+    int64_t id = 0;
+    ntc_job_desc d = {};
+    ntc_job_info info = {};
+    ntc_handle* h = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done_ev = nullptr;   // end of the last enqueued epoch + RMSE
+    bool busy = false;
+    DevMem tidx, tval, scratch;
+    double* host_sum = nullptr;      // pinned: squared residual sum of the last RMSE
+    std::vector<float> factors[ntc::kMaxOrder];   // host copy once done
+};
+
+bool desc_ok(const ntc_job_desc* d, std::string* why) {
+    if (!d) return *why = "null job description", false;
+    if (d->order < 2 || d->order > ntc::kMaxOrder) return *why = "order must be in [2, 8]", false;
+    for (int i = 0; i < d->order; ++i)
+        if (d->dims[i] < 1 || d->dims[i] > INT32_MAX) return *why = "dims must be in [1, 2^31)", false;
+    if (d->rank < 1 || d->rank > 64) return *why = "rank must be in [1, 64]", false;
+    if (!(d->lambda >= 0.0) || !std::isfinite(d->lambda)) return *why = "lambda must be finite and >= 0", false;
+    if (!(d->c > 0.0 && d->c <= 1.0)) return *why = "c must be in (0, 1]", false;
+    if (d->nnz < 1 || !d->idx || !d->vals) return *why = "a job needs observations", false;
+    if (d->n_test < 1 || !d->test_idx || !d->test_vals) return *why = "a job needs held-out observations", false;
+    if (!(d->target_rmse >= 0.0)) return *why = "target_rmse must be >= 0", false;
+    if (d->max_epochs < 1) return *why = "max_epochs must be >= 1", false;
+    if (!std::isfinite(d->arrival)) return *why = "arrival must be finite", false;
+    return true;
+}
+
+// Device bytes of a job, following the allocations of ntc_create,
+// ntc_set_observed and the per-mode plans and scratch of ntc_epoch.
+int64_t model_bytes(const ntc_job_desc* d) {
+    const int N = d->order;
+    const int64_t nnz = d->nnz;
+    const int rp = ntc::pad_rank(d->rank);
+    const int T = rp / 8;
+    const int64_t pw = (int64_t)T * (T + 1) / 2 * 64 + rp;   // floats per reduced-sum row
+    const int64_t ent = (N <= 4 ? 4 : 8) * 4;                 // bytes per bucket entry
+    int64_t sum_dims = 0, max_dim = 0;
+    for (int i = 0; i < N; ++i) {
+        sum_dims += d->dims[i];
+        max_dim = std::max<int64_t>(max_dim, d->dims[i]);
+    }
+    int64_t b = 0;
+    b += nnz * (4 * N + 4);                                   // COO kept for the cost
+    b += N * nnz * ent;                                       // one bucket per mode
+    b += sum_dims * 8 + N * 8;                                // row_ptr
+    b += sum_dims * 8;                                        // row maps
+    b += sum_dims * rp * (4 + (d->storage_bf16 ? 2 : 0));    // masters (+ BF16 copies)
+    b += sum_dims * 8;                                        // light-row plans
+    b += nnz * 4;                                             // visit lists
+    b += nnz + (1 << 20);                                     // candidates and chosen lists
+    const int64_t items = nnz / 16384 + 2 * max_dim + 1;      // chunks + split rows (bound)
+    b += items * pw * 4 * 2;                                  // partials and group sums
+    b += max_dim * pw * 4;                                    // per-row reduced sums
+    b += d->n_test * (4 * N + 4) + ntc::kRmseScratch * 8;    // held-out set
+    b += nnz * (4 * N + 4) + nnz * 16 + (nnz / 256 + 1) * 8;  // admission: COO copy + sort buffers
+    b += 8 << 20;                                             // small buffers and allocation rounding
+    return b;
+}
+
+}  // namespace
+
+struct ntc_server {
+    double budget = 0.0;
+    int max_running = 1;
+    std::vector<std::unique_ptr<Job>> jobs;
+    std::deque<int64_t> queue;   // queued job ids in (arrival, id) order
+    std::chrono::steady_clock::time_point t0;
+    std::string err;
+    ntc_server_stats st = {};
+    cudaStream_t qstream = nullptr;   // prediction queries
+    DevMem q_slot, q_idx, q_out, q_table;
+    int device = 0;
+
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+    ntc_status fail(ntc_status s, const std::string& m) {
+        err = m;
+        return s;
+    }
+};
+
+namespace {
+
+ntc_status cuda_fail(ntc_server* s, cudaError_t e, const char* what) {
+    return s->fail(e == cudaErrorMemoryAllocation ? NTC_ERR_OOM : NTC_ERR_CUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void release_job(ntc_server* s, Job& j) {
+    if (j.h) ntc_destroy(j.h);
+    j.h = nullptr;
+    j.tidx.release();
+    j.tval.release();
+    j.scratch.release();
+    if (j.host_sum) cudaFreeHost(j.host_sum);
+    j.host_sum = nullptr;
+    if (j.done_ev) cudaEventDestroy(j.done_ev);
+    j.done_ev = nullptr;
+    if (j.stream) cudaStreamDestroy(j.stream);
+    j.stream = nullptr;
+    j.busy = false;
+    if (j.info.state == NTC_JOB_RUNNING) {
+        s->st.bytes_in_use -= j.info.bytes;
+        s->st.running -= 1;
+    }
+}
+
+// Keeps the factors on the host, frees the device state, marks the job done.
+ntc_status finish_job(ntc_server* s, Job& j, bool reached) {
+    for (int m = 0; m < j.d.order; ++m) {
+        j.factors[m].resize((size_t)j.d.dims[m] * j.d.rank);
+        ntc_status r = ntc_get_factor(j.h, m, j.factors[m].data());
+        if (r != NTC_OK) return s->fail(r, std::string("job factor download: ") + ntc_last_error(j.h));
+    }
+    release_job(s, j);
+    j.info.state = NTC_JOB_DONE;
+    j.info.reached = reached ? 1 : 0;
+    j.info.t_done = s->now();
+    s->st.done += 1;
+    return NTC_OK;
+}
+
+void fail_job(ntc_server* s, Job& j, const std::string& why) {
+    release_job(s, j);
+    j.info.state = NTC_JOB_FAILED;
+    j.info.t_done = s->now();
+    s->st.failed += 1;
+    s->err = "job " + std::to_string(j.id) + ": " + why;
+}
+
+// Device state of a job: handle, stream, observations, held-out set, initial RMSE.
+ntc_status admit_job(ntc_server* s, Job& j) {
+    const ntc_job_desc& d = j.d;
+    cudaError_t e = cudaStreamCreateWithFlags(&j.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j.done_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&j.host_sum, sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(s, e, "job stream");
+    ntc_status r = ntc_create(d.order, d.dims, d.rank, d.lambda, &j.h);
+    if (r != NTC_OK) return s->fail(r, "ntc_create failed");
+    auto chk = [&](ntc_status q) -> bool {
+        if (q == NTC_OK) return true;
+        r = q;
+        s->err = ntc_last_error(j.h);
+        return false;
+    };
+    if (!chk(ntc_set_stream(j.h, j.stream)) || !chk(ntc_set_param(j.h, "storage_bf16", d.storage_bf16 ? 1.0 : 0.0)) ||
+        !chk(ntc_set_param(j.h, "init_seed", (double)d.init_seed)) ||
+        !chk(ntc_set_observed(j.h, d.nnz, d.idx, d.vals)))
+        return r;
+    for (int64_t q = 0; q < d.n_test * d.order; ++q) {
+        const int32_t v = d.test_idx[q];
+        if (v < 0 || v >= d.dims[q % d.order]) return s->fail(NTC_ERR_INDEX, "a held-out index is out of range");
+    }
+    e = j.tidx.ensure(sizeof(int32_t) * (size_t)(d.n_test * d.order));
+    if (e == cudaSuccess) e = j.tval.ensure(sizeof(float) * (size_t)d.n_test);
+    if (e == cudaSuccess) e = j.scratch.ensure(sizeof(double) * ntc::kRmseScratch);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j.tidx.p, d.test_idx, sizeof(int32_t) * (size_t)(d.n_test * d.order),
+                            cudaMemcpyHostToDevice, j.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j.tval.p, d.test_vals, sizeof(float) * (size_t)d.n_test, cudaMemcpyHostToDevice, j.stream);
+    if (e == cudaSuccess)
+        e = ntc::rmse_enqueue(j.h, j.tidx.as<int32_t>(), j.tval.as<float>(), d.n_test, j.scratch.as<double>(),
+                              j.host_sum);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(j.stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "job admission");
+    j.info.rmse0 = j.info.rmse = std::sqrt(*j.host_sum / (double)d.n_test);
+    return NTC_OK;
+}
+
+ntc_status enqueue_epoch(ntc_server* s, Job& j) {
+    ntc_status r = ntc_epoch(j.h, nullptr, j.d.c, j.d.seed + (uint64_t)j.info.epochs);
+    if (r != NTC_OK) return s->fail(r, ntc_last_error(j.h));
+    cudaError_t e = ntc::rmse_enqueue(j.h, j.tidx.as<int32_t>(), j.tval.as<float>(), j.d.n_test,
+                                      j.scratch.as<double>(), j.host_sum);
+    if (e == cudaSuccess) e = cudaEventRecord(j.done_ev, j.stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "epoch enqueue");
+    j.busy = true;
+    return NTC_OK;
+}
+
+Job* find_job(const ntc_server* s, int64_t id) {
+    if (!s || id < 0 || id >= (int64_t)s->jobs.size()) return nullptr;
+    return s->jobs[(size_t)id].get();
+}
+
+}  // namespace
+
+extern "C" {
+
+ntc_status ntc_job_bytes(const ntc_job_desc* desc, int64_t* out) {
+    std::string why;
+    if (!out || !desc_ok(desc, &why)) return NTC_ERR_ARG;
+    *out = model_bytes(desc);
+    return NTC_OK;
+}
+
+ntc_status ntc_server_create(double hbm_budget, int max_running, ntc_server** out) {
+    if (!out) return NTC_ERR_ARG;
+    *out = nullptr;
+    if (!(hbm_budget > 0.0) || !std::isfinite(hbm_budget) || max_running < 1) return NTC_ERR_ARG;
+    auto s = std::make_unique<ntc_server>();
+    s->budget = hbm_budget;
+    s->max_running = max_running;
+    s->t0 = std::chrono::steady_clock::now();
+    if (cudaGetDevice(&s->device) != cudaSuccess) return NTC_ERR_CUDA;
+    if (cudaStreamCreateWithFlags(&s->qstream, cudaStreamNonBlocking) != cudaSuccess) return NTC_ERR_CUDA;
+    *out = s.release();
+    return NTC_OK;
+}
+
+ntc_status ntc_server_submit(ntc_server* s, const ntc_job_desc* desc, int64_t* job_id) {
+    if (!s || !job_id) return NTC_ERR_ARG;
+    std::string why;
+    if (!desc_ok(desc, &why)) return s->fail(NTC_ERR_ARG, why);
+    const int64_t bytes = model_bytes(desc);
+    if ((double)bytes > s->budget) return s->fail(NTC_ERR_ARG, "job needs more than the whole budget");
+    auto j = std::make_unique<Job>();
+    j->id = (int64_t)s->jobs.size();
+    j->d = *desc;
+    j->info.state = NTC_JOB_QUEUED;
+    j->info.rmse = j->info.rmse0 = -1.0;
+    j->info.t_arrival = desc->arrival;
+    j->info.t_admit = j->info.t_done = -1.0;
+    j->info.bytes = bytes;
+    // arrival order, ties by id
+    auto pos = std::upper_bound(s->queue.begin(), s->queue.end(), desc->arrival,
+                                [&](double t, int64_t id) { return t < s->jobs[(size_t)id]->d.arrival; });
+    s->queue.insert(pos, j->id);
+    *job_id = j->id;
+    s->jobs.push_back(std::move(j));
+    s->st.submitted += 1;
+    s->st.queued += 1;
+    return NTC_OK;
+}
+
+ntc_status ntc_server_step(ntc_server* s, int64_t* running, int64_t* queued) {
+    if (!s) return NTC_ERR_ARG;
+    if (cudaSetDevice(s->device) != cudaSuccess) return s->fail(NTC_ERR_CUDA, "cudaSetDevice");
+    // 1. finished epochs
+    for (auto& jp : s->jobs) {
+        Job& j = *jp;
+        if (j.info.state != NTC_JOB_RUNNING || !j.busy) continue;
+        const cudaError_t q = cudaEventQuery(j.done_ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) {
+            fail_job(s, j, std::string("epoch: ") + cudaGetErrorString(q));
+            return NTC_ERR_CUDA;
+        }
+        j.busy = false;
+        j.info.epochs += 1;
+        j.info.rmse = std::sqrt(*j.host_sum / (double)j.d.n_test);
+        s->st.epochs += 1;
+        s->st.entries += j.d.nnz;
+        if (!(j.info.rmse > j.d.target_rmse) || j.info.epochs >= j.d.max_epochs) {
+            const bool reached = !(j.info.rmse > j.d.target_rmse);
+            ntc_status r = finish_job(s, j, reached);
+            if (r != NTC_OK) return r;
+        }
+    }
+    // 2. admission: head of the queue first, while it has arrived and fits
+    const double t = s->now();
+    while (!s->queue.empty()) {
+        Job& j = *s->jobs[(size_t)s->queue.front()];
+        if (j.d.arrival > t || s->st.running >= s->max_running) break;
+        if ((double)(s->st.bytes_in_use + j.info.bytes) > s->budget) break;
+        s->queue.pop_front();
+        s->st.queued -= 1;
+        ntc_status r = admit_job(s, j);
+        if (r != NTC_OK) {
+            const std::string why = s->err;
+            fail_job(s, j, why);
+            continue;
+        }
+        j.info.state = NTC_JOB_RUNNING;
+        j.info.t_admit = s->now();
+        s->st.running += 1;
+        s->st.bytes_in_use += j.info.bytes;
+        s->st.peak_bytes = std::max(s->st.peak_bytes, s->st.bytes_in_use);
+        s->st.peak_running = std::max(s->st.peak_running, s->st.running);
+        if (!(j.info.rmse > j.d.target_rmse)) {   // already at the target
+            ntc_status r2 = finish_job(s, j, true);
+            if (r2 != NTC_OK) return r2;
+        }
+    }
+    // 3. next epoch of every idle running job
+    for (auto& jp : s->jobs) {
+        Job& j = *jp;
+        if (j.info.state != NTC_JOB_RUNNING || j.busy) continue;
+        ntc_status r = enqueue_epoch(s, j);
+        if (r != NTC_OK) {
+            const std::string why = s->err;
+            fail_job(s, j, why);
+            return r;
+        }
+    }
+    if (running) *running = s->st.running;
+    if (queued) *queued = s->st.queued;
+    return NTC_OK;
+}
+
+ntc_status ntc_server_sync(ntc_server* s) {
+    if (!s) return NTC_ERR_ARG;
+    for (auto& jp : s->jobs)
+        if (jp->info.state == NTC_JOB_RUNNING && jp->stream) {
+            const cudaError_t e = cudaStreamSynchronize(jp->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "job stream");
+        }
+    return NTC_OK;
+}
+
+double ntc_server_now(const ntc_server* s) { return s ? s->now() : -1.0; }
+
+ntc_status ntc_server_job_info(const ntc_server* s, int64_t job_id, ntc_job_info* out) {
+    const Job* j = find_job(s, job_id);
+    if (!j || !out) return NTC_ERR_ARG;
+    *out = j->info;
+    return NTC_OK;
+}
+
+ntc_status ntc_server_predict(ntc_server* s, int64_t n, const int64_t* job_ids, const int32_t* idx, float* out) {
+    if (!s || n < 0 || (n > 0 && (!job_ids || !idx || !out))) return NTC_ERR_ARG;
+    if (n == 0) return NTC_OK;
+    // the running jobs named by the queries, each once, in first-use order
+    std::vector<int32_t> slot((size_t)n);
+    std::vector<ntc_handle*> hs;
+    std::vector<int64_t> slot_of(s->jobs.size(), -1);
+    for (int64_t q = 0; q < n; ++q) {
+        Job* j = find_job(s, job_ids[q]);
+        if (!j) return s->fail(NTC_ERR_ARG, "unknown job id");
+        if (j->info.state != NTC_JOB_RUNNING) return s->fail(NTC_ERR_STATE, "query to a job that is not running");
+        for (int i = 0; i < j->d.order; ++i) {
+            const int32_t v = idx[q * ntc::kMaxOrder + i];
+            if (v < 0 || v >= j->d.dims[i]) return s->fail(NTC_ERR_INDEX, "a query index is out of range");
+        }
+        int64_t& sl = slot_of[(size_t)j->id];
+        if (sl < 0) {
+            sl = (int64_t)hs.size();
+            hs.push_back(j->h);
+            // the query reads the factors after the job's enqueued epoch
+            const cudaError_t e = cudaStreamWaitEvent(s->qstream, j->done_ev, 0);
+            if (e != cudaSuccess) return cuda_fail(s, e, "query wait");
+        }
+        slot[(size_t)q] = (int32_t)sl;
+    }
+    cudaError_t e = s->q_slot.ensure(sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = s->q_idx.ensure(sizeof(int32_t) * (size_t)n * ntc::kMaxOrder);
+    if (e == cudaSuccess) e = s->q_out.ensure(sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = s->q_table.ensure(ntc::factor_table_bytes() * hs.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->q_slot.p, slot.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s->qstream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->q_idx.p, idx, sizeof(int32_t) * (size_t)n * ntc::kMaxOrder, cudaMemcpyHostToDevice,
+                            s->qstream);
+    if (e == cudaSuccess)
+        e = ntc::predict_multi(hs.data(), (int)hs.size(), s->q_slot.as<int32_t>(), s->q_idx.as<int32_t>(), n,
+                               s->q_out.as<float>(), s->q_table.p, s->qstream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, s->q_out.p, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s->qstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->qstream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "predict");
+    s->st.predict_calls += 1;
+    s->st.predict_queries += n;
+    s->st.predict_launches += 1;
+    return NTC_OK;
+}
+
+ntc_status ntc_server_get_factor(ntc_server* s, int64_t job_id, int mode, float* out) {
+    Job* j = find_job(s, job_id);
+    if (!j || !out || mode < 0 || mode >= (j ? j->d.order : 0)) return NTC_ERR_ARG;
+    if (j->info.state == NTC_JOB_RUNNING) {
+        const ntc_status r = ntc_get_factor(j->h, mode, out);
+        if (r != NTC_OK) return s->fail(r, ntc_last_error(j->h));
+        return NTC_OK;
+    }
+    if (j->info.state != NTC_JOB_DONE) return s->fail(NTC_ERR_STATE, "the job has no factors yet");
+    std::copy(j->factors[mode].begin(), j->factors[mode].end(), out);
+    return NTC_OK;
+}
+
+ntc_status ntc_server_stats_get(const ntc_server* s, ntc_server_stats* out) {
+    if (!s || !out) return NTC_ERR_ARG;
+    *out = s->st;
+    return NTC_OK;
+}
+
+const char* ntc_server_last_error(const ntc_server* s) { return s ? s->err.c_str() : "null server"; }
+
+void ntc_server_destroy(ntc_server* s) {
+    if (!s) return;
+    for (auto& jp : s->jobs) {
+        if (jp->stream) cudaStreamSynchronize(jp->stream);
+        release_job(s, *jp);
+    }
+    if (s->qstream) cudaStreamDestroy(s->qstream);
+    delete s;
+}
+
+}  // extern "C"

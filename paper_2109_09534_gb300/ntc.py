@@ -1,4 +1,4 @@
-"""Thin ctypes binding of the C ABI in ``include/ntc.h``.
+"""Thin ctypes binding of the C ABI in ``include/ntc.h`` and ``include/ntc_serve.h``.
 
 Argument marshalling only: every step of the method runs in the CUDA library
 ``libntc.so``.  The functions keep the C names; :class:`NTC` wraps a handle
@@ -9,6 +9,7 @@ the library is missing or a call fails, an exception is raised.
 from __future__ import annotations
 
 import ctypes
+import glob
 import os
 import re
 from typing import Optional, Sequence
@@ -19,6 +20,7 @@ from . import build as _build
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ntc.h")
+HEADERS = sorted(glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
 
 NTC_OK, NTC_ERR_ARG, NTC_ERR_INDEX, NTC_ERR_OOM, NTC_ERR_STATE, NTC_ERR_CUDA = range(6)
 KERNELS = ["light", "heavy_sample", "heavy_resolve", "heavy_gram", "finish"]
@@ -39,14 +41,39 @@ class ntc_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64)]
 
 
+class ntc_job_desc(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("dims", ctypes.c_int64 * 8), ("rank", ctypes.c_int),
+                ("lam", ctypes.c_double), ("c", ctypes.c_double), ("storage_bf16", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("init_seed", ctypes.c_uint64), ("nnz", ctypes.c_int64),
+                ("idx", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("n_test", ctypes.c_int64),
+                ("test_idx", ctypes.c_void_p), ("test_vals", ctypes.c_void_p),
+                ("target_rmse", ctypes.c_double), ("max_epochs", ctypes.c_int), ("arrival", ctypes.c_double)]
+
+
+class ntc_job_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("reached", ctypes.c_int), ("epochs", ctypes.c_int),
+                ("rmse", ctypes.c_double), ("rmse0", ctypes.c_double), ("t_arrival", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("bytes", ctypes.c_int64)]
+
+
+class ntc_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ["submitted", "queued", "running", "done", "failed", "bytes_in_use", "peak_bytes", "peak_running",
+                 "epochs", "entries", "predict_calls", "predict_queries", "predict_launches"]]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = range(4)
+
 _lib = None
 
 
 def declared_functions() -> list:
-    """Names of the functions declared in include/ntc.h."""
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ntc_[a-z_]+)\s*\(", src)))
+    """Names of the functions declared in include/*.h."""
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(ntc_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def load(path: Optional[str] = None):
@@ -82,6 +109,15 @@ def load(path: Optional[str] = None):
         "ntc_sample_mask": [P, i32, dbl, u64, u64, i32, P],
         "ntc_get_profile": [P, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "ntc_measure_fp32_peak": [P, ctypes.POINTER(dbl)],
+        "ntc_job_bytes": [ctypes.POINTER(ntc_job_desc), ctypes.POINTER(i64)],
+        "ntc_server_create": [dbl, i32, ctypes.POINTER(P)],
+        "ntc_server_submit": [P, ctypes.POINTER(ntc_job_desc), ctypes.POINTER(i64)],
+        "ntc_server_step": [P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "ntc_server_sync": [P],
+        "ntc_server_job_info": [P, i64, ctypes.POINTER(ntc_job_info)],
+        "ntc_server_predict": [P, i64, P, P, P],
+        "ntc_server_get_factor": [P, i64, i32, P],
+        "ntc_server_stats_get": [P, ctypes.POINTER(ntc_server_stats)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -91,6 +127,12 @@ def load(path: Optional[str] = None):
     L.ntc_last_error.restype = ctypes.c_char_p
     L.ntc_destroy.argtypes = [P]
     L.ntc_destroy.restype = None
+    L.ntc_server_now.argtypes = [P]
+    L.ntc_server_now.restype = dbl
+    L.ntc_server_last_error.argtypes = [P]
+    L.ntc_server_last_error.restype = ctypes.c_char_p
+    L.ntc_server_destroy.argtypes = [P]
+    L.ntc_server_destroy.restype = None
     _lib = L
     return L
 
@@ -250,3 +292,100 @@ class NTC:
         _check(self.h, self.L.ntc_sample_mask(self.h, int(mode), float(c), int(seed), int(ao_iter),
                                               int(inner), _ptr(m)))
         return m[:nnz]
+
+
+# ---------------------------------------------------------------------------
+# Completion server (include/ntc_serve.h)
+
+def job_desc(dims, rank, lam, c, idx, vals, test_idx, test_vals, target_rmse, max_epochs, arrival=0.0,
+             seed=1, init_seed=3, storage_bf16=0) -> ntc_job_desc:
+    """An ntc_job_desc over numpy arrays (the caller keeps them alive)."""
+    d = ntc_job_desc()
+    d.order = len(dims)
+    for i, n in enumerate(dims):
+        d.dims[i] = int(n)
+    d.rank, d.lam, d.c, d.storage_bf16 = int(rank), float(lam), float(c), int(storage_bf16)
+    d.seed, d.init_seed = int(seed), int(init_seed)
+    d.nnz, d.idx, d.vals = len(vals), idx.ctypes.data, vals.ctypes.data
+    d.n_test, d.test_idx, d.test_vals = len(test_vals), test_idx.ctypes.data, test_vals.ctypes.data
+    d.target_rmse, d.max_epochs, d.arrival = float(target_rmse), int(max_epochs), float(arrival)
+    return d
+
+
+def job_bytes(d: ntc_job_desc) -> int:
+    out = ctypes.c_int64()
+    _check(None, load().ntc_job_bytes(ctypes.byref(d), ctypes.byref(out)))
+    return out.value
+
+
+class Server:
+    """Continuous-batching completion server on the current CUDA device."""
+
+    def __init__(self, hbm_budget: float, max_running: int = 64):
+        L = load()
+        self._s = ctypes.c_void_p()
+        st = L.ntc_server_create(float(hbm_budget), int(max_running), ctypes.byref(self._s))
+        if st != NTC_OK:
+            raise NTCError(st, "ntc_server_create failed")
+        self._keep = {}
+
+    def _check(self, status: int) -> None:
+        if status != NTC_OK:
+            raise NTCError(status, (load().ntc_server_last_error(self._s) or b"").decode())
+
+    def close(self) -> None:
+        if self._s:
+            load().ntc_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, dims, rank, lam, c, idx, vals, test_idx, test_vals, target_rmse, max_epochs,
+               arrival=0.0, seed=1, init_seed=3, storage_bf16=0) -> int:
+        arrays = [np.ascontiguousarray(idx, dtype=np.int32), np.ascontiguousarray(vals, dtype=np.float32),
+                  np.ascontiguousarray(test_idx, dtype=np.int32), np.ascontiguousarray(test_vals, dtype=np.float32)]
+        d = job_desc(dims, rank, lam, c, *arrays, target_rmse, max_epochs, arrival, seed, init_seed, storage_bf16)
+        jid = ctypes.c_int64()
+        self._check(load().ntc_server_submit(self._s, ctypes.byref(d), ctypes.byref(jid)))
+        self._keep[jid.value] = arrays   # read at admission
+        return jid.value
+
+    def step(self):
+        r, q = ctypes.c_int64(), ctypes.c_int64()
+        self._check(load().ntc_server_step(self._s, ctypes.byref(r), ctypes.byref(q)))
+        for jid in [j for j in self._keep if self.job_info(j)["state"] != JOB_QUEUED]:
+            del self._keep[jid]
+        return r.value, q.value
+
+    def sync(self) -> None:
+        self._check(load().ntc_server_sync(self._s))
+
+    def now(self) -> float:
+        return load().ntc_server_now(self._s)
+
+    def job_info(self, jid: int) -> dict:
+        out = ntc_job_info()
+        self._check(load().ntc_server_job_info(self._s, int(jid), ctypes.byref(out)))
+        return {f: getattr(out, f) for f, _ in ntc_job_info._fields_}
+
+    def predict(self, job_ids, idx) -> np.ndarray:
+        """idx: [n][order] (padded to 8 columns here) for the jobs named in job_ids."""
+        job_ids = np.ascontiguousarray(job_ids, dtype=np.int64)
+        idx = np.asarray(idx, dtype=np.int32)
+        q = np.zeros((len(job_ids), 8), dtype=np.int32)
+        q[:, :idx.shape[1]] = idx
+        out = np.empty(len(job_ids), dtype=np.float32)
+        self._check(load().ntc_server_predict(self._s, len(job_ids), _ptr(job_ids), _ptr(q), _ptr(out)))
+        return out
+
+    def get_factor(self, jid: int, mode: int, rows: int, rank: int) -> np.ndarray:
+        out = np.empty((rows, rank), dtype=np.float32)
+        self._check(load().ntc_server_get_factor(self._s, int(jid), int(mode), _ptr(out)))
+        return out
+
+    def stats(self) -> dict:
+        out = ntc_server_stats()
+        self._check(load().ntc_server_stats_get(self._s, ctypes.byref(out)))
+        return {f: getattr(out, f) for f, _ in ntc_server_stats._fields_}

@@ -191,3 +191,46 @@ def random_factors(dims: Sequence[int], rank: int, scale: float, seed: int) -> L
     float32 and a float64 implementation start from identical numbers."""
     rng = np.random.default_rng(seed)
     return [(rng.random((d, rank)) * scale).astype(np.float32).astype(np.float64) for d in dims]
+
+
+# ---- the serving stream ------------------------------------------------------
+
+@dataclasses.dataclass
+class JobSpec:
+    """One job of a serving stream; its data come from make_problem(seed=data_seed)."""
+    arrival: float
+    dims: List[int]
+    rank: int
+    nnz: int
+    storage_bf16: int
+    data_seed: int
+
+
+def serving_stream(n_jobs: int = 256, rate: float = 4.0, dim_range=(1_000, 200_000),
+                   nnz_range=(1_000_000, 50_000_000), ranks=(8, 16, 32, 64), orders=(3, 4),
+                   seed: int = 5) -> List[JobSpec]:
+    """Poisson arrivals (mean `rate` jobs/s) of completion jobs: order drawn
+    from `orders`, each mode size log-uniform in dim_range, rank from `ranks`,
+    observation count log-uniform in nnz_range, FP32 and BF16 storage
+    alternating (half each)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for j in range(n_jobs):
+        t += rng.exponential(1.0 / rate)
+        N = int(rng.choice(orders))
+        lo, hi = math.log(dim_range[0]), math.log(dim_range[1])
+        dims = [int(round(math.exp(rng.uniform(lo, hi)))) for _ in range(N)]
+        rank = int(rng.choice(ranks))
+        nnz = int(round(math.exp(rng.uniform(math.log(nnz_range[0]), math.log(nnz_range[1])))))
+        out.append(JobSpec(arrival=t, dims=dims, rank=rank, nnz=nnz, storage_bf16=j % 2,
+                           data_seed=seed * 1_000_003 + j))
+    return out
+
+
+def serving_job(spec: JobSpec, sigma: float = 0.01, test_frac: float = 0.01) -> Problem:
+    """Planted U[0,1] factors of the spec's rank, uniform observed indices,
+    Gaussian noise sigma, lambda = 1e-3, c = 0.1."""
+    return make_problem(spec.dims, spec.rank, spec.nnz, lam=1e-3, c=0.1, index_dist="uniform",
+                        sigma=sigma, test_frac=test_frac, seed=spec.data_seed,
+                        name=f"job-{len(spec.dims)}way-R{spec.rank}-{spec.nnz}")
