@@ -384,11 +384,13 @@ def run_serve(args):
     while True:
         srv.step()
         now = srv.now()
-        # queries that arrived since the last tick (Poisson), against running jobs
-        nq = rng.poisson(args.serve_qps * (now - t_q))
-        pending += list(np.sort(rng.uniform(t_q, now, nq)))
-        t_q = now
+        # queries that arrived since the last tick (Poisson), against running
+        # jobs: while none is running there is nothing to query
         running = [(j, probs[j]) for j in ids if srv.job_info(j)["state"] == ntc.JOB_RUNNING]
+        if running:
+            nq = rng.poisson(args.serve_qps * (now - t_q))
+            pending += list(np.sort(rng.uniform(t_q, now, nq)))
+        t_q = now
         if pending and running:
             pick = rng.integers(0, len(running), len(pending))
             q_job = np.array([j for j, _ in running], dtype=np.int64)[pick]
@@ -419,6 +421,10 @@ def run_serve(args):
                                  "queries": st["predict_queries"], "launches": st["predict_launches"]},
             "entries_per_s": st["entries"] / wall, "epochs": st["epochs"], "wall_s": wall,
             "peak_running": st["peak_running"], "peak_bytes": st["peak_bytes"], "budget_bytes": args.serve_budget,
+            "job_results": [{"order": len(s.dims), "rank": s.rank, "nnz": s.nnz, "bf16": s.storage_bf16,
+                             "epochs": i["epochs"], "rmse0": round(i["rmse0"], 5), "rmse": round(i["rmse"], 5),
+                             "reached": i["reached"], "queue_s": round(i["t_admit"] - i["t_arrival"], 4),
+                             "run_s": round(i["t_done"] - i["t_admit"], 4)} for s, i in zip(specs, infos)],
             "n_gpus": 1, "data": "synthetic", "dtype": "f32 / bf16-storage (half the jobs each)", "clocks": clk,
             "config": {"workload": f"{args.serve_jobs} jobs, Poisson {args.serve_rate}/s, order 3-4, mode sizes "
                                    f"log-uniform {args.serve_dims}, R in 8/16/32/64, observations log-uniform "

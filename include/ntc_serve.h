@@ -94,12 +94,15 @@ ntc_status ntc_server_create(double hbm_budget, int max_running, ntc_server** ou
  * NTC_ERR_ARG for an invalid description or a job larger than the budget. */
 ntc_status ntc_server_submit(ntc_server* s, const ntc_job_desc* desc, int64_t* job_id);
 
-/* One scheduler tick: collect finished epochs (read their RMSE, mark jobs done
- * and free them), admit queued jobs whose arrival time has passed while the
- * budget and max_running allow (in arrival order, the head of the queue
- * first), and enqueue the next epoch of every running job that is idle.
- * Does not wait for the GPU.  *running / *queued (may be NULL) get the counts
- * after the tick. */
+/* One scheduler tick: take over jobs whose admission finished, collect
+ * finished epochs (read their RMSE, mark jobs done and free them), start the
+ * admission of queued jobs whose arrival time has passed while the budget and
+ * max_running allow (in arrival order, the head of the queue first; the job's
+ * memory counts from here, its upload and bucketing run on a worker thread and
+ * the job is RUNNING from the first tick after they finish), and enqueue the
+ * next epoch of every running job that is idle.  Does not wait for the GPU.
+ * *running (admitted jobs, admitting included) / *queued (may be NULL) get the
+ * counts after the tick. */
 ntc_status ntc_server_step(ntc_server* s, int64_t* running, int64_t* queued);
 
 /* Blocks until every running job has finished its enqueued epoch (a tick
@@ -113,14 +116,17 @@ ntc_status ntc_server_job_info(const ntc_server* s, int64_t job_id, ntc_job_info
 
 /* n queries: job_ids[q] names a running job and idx[q * 8 + i] (i < that job's
  * order) its zero-based index; out[q] gets the CP model value (eq. 1) from
- * the job's current factors.  One kernel launch serves all jobs of the call.
+ * the job's factors after its last collected epoch (a snapshot, so a query
+ * never waits for an epoch in flight).  One kernel launch on a high-priority
+ * stream serves all jobs of the call.
  * NTC_ERR_STATE if a job is not running, NTC_ERR_INDEX for an index out of
  * range.  Synchronous (out is host memory). */
 ntc_status ntc_server_predict(ntc_server* s, int64_t n, const int64_t* job_ids, const int32_t* idx, float* out);
 
-/* Factor `mode` of a job, [dims[mode]][rank] row-major FP32: from the device
- * while running (waits for the job's enqueued work), from the host copy once
- * done.  NTC_ERR_STATE while queued. */
+/* Factor `mode` of a job, [dims[mode]][rank] row-major FP32, the same factors
+ * queries see: while running, those after the last epoch a tick collected (the
+ * query snapshot; an epoch in flight is not waited for); once done, the final
+ * factors (host copy).  NTC_ERR_STATE while queued or admitting. */
 ntc_status ntc_server_get_factor(ntc_server* s, int64_t job_id, int mode, float* out);
 
 ntc_status ntc_server_stats_get(const ntc_server* s, ntc_server_stats* out);

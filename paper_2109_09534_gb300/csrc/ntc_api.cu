@@ -518,15 +518,49 @@ cudaError_t rmse_enqueue(ntc_handle* h, const int32_t* idx, const float* vals, i
 
 size_t factor_table_bytes() { return sizeof(FactorSet); }
 
-cudaError_t predict_multi(ntc_handle* const* handles, int nh, const int32_t* slot, const int32_t* idx, int64_t n,
-                          float* out, void* table, cudaStream_t s) {
+int64_t snapshot_floats(const ntc_handle* h) {
+    int64_t n = 0;
+    for (int i = 0; i < h->order; ++i) n += h->dims[i] * h->rp;
+    return n;
+}
+
+cudaError_t snapshot_factors(ntc_handle* h, float* dst) {
+    for (int i = 0; i < h->order; ++i) {
+        const size_t b = sizeof(float) * (size_t)(h->dims[i] * h->rp);
+        const cudaError_t e = cudaMemcpyAsync(dst, h->U[i].p, b, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return e;
+        dst += h->dims[i] * h->rp;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t predict_multi(ntc_handle* const* handles, const float* const* snaps, int nh, const int32_t* slot,
+                          const int32_t* idx, int64_t n, float* out, void* table, cudaStream_t s) {
     std::vector<FactorSet> t((size_t)nh);
-    for (int j = 0; j < nh; ++j) t[(size_t)j] = factor_set(handles[j]);
+    for (int j = 0; j < nh; ++j) {
+        t[(size_t)j] = factor_set(handles[j]);
+        if (snaps[j]) {
+            const float* p = snaps[j];
+            for (int i = 0; i < handles[j]->order; ++i) {
+                t[(size_t)j].U[i] = p;
+                p += handles[j]->dims[i] * handles[j]->rp;
+            }
+        }
+    }
     // pageable source: the copy is staged before the call returns
     cudaError_t e = cudaMemcpyAsync(table, t.data(), sizeof(FactorSet) * (size_t)nh, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess || n == 0) return e;
     k_predict_multi<<<grid_for(n), 256, 0, s>>>(static_cast<const FactorSet*>(table), slot, idx, n, out);
     return cudaGetLastError();
+}
+
+ntc_status prepare_epoch(ntc_handle* h, double c) {
+    ntc_status st = check_ready(h);
+    if (st != NTC_OK) return st;
+    if (!(c > 0.0 && c <= 1.0)) return fail(h, NTC_ERR_ARG, "c must be in (0, 1]");
+    for (int i = 0; i < h->order; ++i)
+        if ((st = build_plan(h, i, c)) != NTC_OK) return st;
+    return reset_stats(h);
 }
 
 int64_t handle_device_bytes(const ntc_handle* h) {

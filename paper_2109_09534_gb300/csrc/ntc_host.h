@@ -169,12 +169,21 @@ constexpr int kRmseScratch = 1025;
 cudaError_t rmse_enqueue(ntc_handle* h, const int32_t* idx, const float* vals, int64_t n, double* scratch,
                          double* host_sum);
 // CP model values for n queries over several handles in one kernel launch on
-// stream s: query e uses handles[slot[e]] and idx[e * kMaxOrder ...]; table
-// is device memory for nh factor tables (>= nh * factor_table_bytes()).
+// stream s: query e uses handles[slot[e]] and idx[e * kMaxOrder ...].  The
+// factors are read from snaps[j] when it is not null (all modes of handle j,
+// mode m at offset sum_{i<m} dims[i] * rp floats, as snapshot_factors writes
+// them), else from the handle's masters.  table is device memory for nh factor
+// tables (>= nh * factor_table_bytes()).
 size_t factor_table_bytes();
-cudaError_t predict_multi(ntc_handle* const* handles, int nh, const int32_t* slot, const int32_t* idx, int64_t n,
-                          float* out, void* table, cudaStream_t s);
+cudaError_t predict_multi(ntc_handle* const* handles, const float* const* snaps, int nh, const int32_t* slot,
+                          const int32_t* idx, int64_t n, float* out, void* table, cudaStream_t s);
+// Copies every mode's FP32 masters into dst (layout above) on the handle's stream.
+cudaError_t snapshot_factors(ntc_handle* h, float* dst);
+int64_t snapshot_floats(const ntc_handle* h);
 // Device bytes the handle holds now.
 int64_t handle_device_bytes(const ntc_handle* h);
+// Builds every mode's plan for minibatch fraction c and sizes the epoch
+// scratch, so that the first ntc_epoch at c allocates nothing.
+ntc_status prepare_epoch(ntc_handle* h, double c);
 
 }  // namespace ntc

@@ -2,16 +2,23 @@
 //
 // Each admitted job owns an ntc_handle (its bucketed observations, factors
 // and scratch stay on the device) and a non-blocking CUDA stream.  A tick
-// collects finished epochs, admits queued jobs under the HBM budget, and
-// enqueues one epoch plus a device RMSE reduction for every idle job; the
-// epochs of different jobs then run concurrently on the GPU.  Prediction
-// queries over many jobs go to one multi-job kernel launch.
+// collects finished epochs, starts the admission of queued jobs under the HBM
+// budget (upload and bucketing run on a worker thread, so ticks and queries
+// go on meanwhile), and enqueues one epoch plus a device RMSE reduction for
+// every idle job; the epochs of different jobs then run concurrently on the
+// GPU.  After each epoch the job's stream copies its factors into one of two
+// snapshot buffers; prediction queries read the snapshot of the last collected
+// epoch (the epoch in flight writes the other one), so they never wait for a
+// job's epoch, and all jobs' queries of a call go to one multi-job launch on a
+// high-priority stream.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <deque>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ntc_serve.h"
@@ -30,8 +37,19 @@ struct Job {
     cudaEvent_t done_ev = nullptr;   // end of the last enqueued epoch + RMSE
     bool busy = false;
     DevMem tidx, tval, scratch;
+    DevMem snap[2];                  // factors after epoch e in snap[e % 2]
     double* host_sum = nullptr;      // pinned: squared residual sum of the last RMSE
     std::vector<float> factors[ntc::kMaxOrder];   // host copy once done
+    // admission on a worker thread: 0 idle, 1 running, 2 succeeded, 3 failed
+    bool admitting = false;
+    std::thread admit_thread;
+    std::atomic<int> admit_state{0};
+    ntc_status admit_status = NTC_OK;
+    std::string admit_err;
+    // device memory of a finished job is freed on a reaper thread (cudaFree
+    // synchronizes the device); its bytes stay in the budget until then
+    std::thread reap_thread;
+    std::atomic<int> reap_state{0};   // 0 none, 1 freeing, 2 freed
 };
 
 bool desc_ok(const ntc_job_desc* d, std::string* why) {
@@ -77,6 +95,7 @@ int64_t model_bytes(const ntc_job_desc* d) {
     b += items * pw * 4 * 2;                                  // partials and group sums
     b += max_dim * pw * 4;                                    // per-row reduced sums
     b += d->n_test * (4 * N + 4) + ntc::kRmseScratch * 8;    // held-out set
+    b += 2 * sum_dims * rp * 4;                               // two factor snapshots for queries
     b += nnz * (4 * N + 4) + nnz * 16 + (nnz / 256 + 1) * 8;  // admission: COO copy + sort buffers
     b += 8 << 20;                                             // small buffers and allocation rounding
     return b;
@@ -110,22 +129,49 @@ ntc_status cuda_fail(ntc_server* s, cudaError_t e, const char* what) {
                    std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-void release_job(ntc_server* s, Job& j) {
+// Frees the job's device state (and its stream); touches only the job.
+void free_device(Job& j) {
+    if (j.stream) cudaStreamSynchronize(j.stream);
     if (j.h) ntc_destroy(j.h);
     j.h = nullptr;
     j.tidx.release();
     j.tval.release();
     j.scratch.release();
+    j.snap[0].release();
+    j.snap[1].release();
     if (j.host_sum) cudaFreeHost(j.host_sum);
     j.host_sum = nullptr;
     if (j.done_ev) cudaEventDestroy(j.done_ev);
     j.done_ev = nullptr;
     if (j.stream) cudaStreamDestroy(j.stream);
     j.stream = nullptr;
+}
+
+// The job stops running; its device memory is freed on a reaper thread and
+// its bytes leave the budget when a tick sees that finished.
+void release_job(ntc_server* s, Job& j) {
     j.busy = false;
-    if (j.info.state == NTC_JOB_RUNNING) {
-        s->st.bytes_in_use -= j.info.bytes;
-        s->st.running -= 1;
+    if (j.info.state == NTC_JOB_RUNNING || j.admitting) s->st.running -= 1;
+    j.admitting = false;
+    j.reap_state.store(1);
+    Job* jp = &j;
+    const int dev = s->device;
+    j.reap_thread = std::thread([jp, dev] {
+        cudaSetDevice(dev);
+        free_device(*jp);
+        jp->reap_state.store(2, std::memory_order_release);
+    });
+}
+
+void collect_reaped(ntc_server* s, bool wait) {
+    for (auto& jp : s->jobs) {
+        Job& j = *jp;
+        if (j.reap_state.load(std::memory_order_acquire) == 0) continue;
+        if (j.reap_state.load(std::memory_order_acquire) == 1 && !wait) continue;
+        if (j.reap_thread.joinable()) {
+            j.reap_thread.join();
+            s->st.bytes_in_use -= j.info.bytes;
+        }
     }
 }
 
@@ -152,42 +198,53 @@ void fail_job(ntc_server* s, Job& j, const std::string& why) {
     s->err = "job " + std::to_string(j.id) + ": " + why;
 }
 
-// Device state of a job: handle, stream, observations, held-out set, initial RMSE.
-ntc_status admit_job(ntc_server* s, Job& j) {
+// Device state of a job: handle, stream, observations, held-out set, initial
+// RMSE and the snapshot of the initial factors.  Runs on the admission worker
+// thread: it touches only the job.
+ntc_status admit_job(Job& j, int device) {
     const ntc_job_desc& d = j.d;
-    cudaError_t e = cudaStreamCreateWithFlags(&j.stream, cudaStreamNonBlocking);
+    auto cuda_err = [&](cudaError_t e, const char* what) {
+        j.admit_err = std::string(what) + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? NTC_ERR_OOM : NTC_ERR_CUDA;
+    };
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&j.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j.done_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&j.host_sum, sizeof(double));
-    if (e != cudaSuccess) return cuda_fail(s, e, "job stream");
+    if (e != cudaSuccess) return cuda_err(e, "job stream");
     ntc_status r = ntc_create(d.order, d.dims, d.rank, d.lambda, &j.h);
-    if (r != NTC_OK) return s->fail(r, "ntc_create failed");
+    if (r != NTC_OK) return j.admit_err = "ntc_create failed", r;
     auto chk = [&](ntc_status q) -> bool {
         if (q == NTC_OK) return true;
         r = q;
-        s->err = ntc_last_error(j.h);
+        j.admit_err = ntc_last_error(j.h);
         return false;
     };
     if (!chk(ntc_set_stream(j.h, j.stream)) || !chk(ntc_set_param(j.h, "storage_bf16", d.storage_bf16 ? 1.0 : 0.0)) ||
         !chk(ntc_set_param(j.h, "init_seed", (double)d.init_seed)) ||
-        !chk(ntc_set_observed(j.h, d.nnz, d.idx, d.vals)))
+        !chk(ntc_set_observed(j.h, d.nnz, d.idx, d.vals)) || !chk(ntc::prepare_epoch(j.h, d.c)))
         return r;
     for (int64_t q = 0; q < d.n_test * d.order; ++q) {
         const int32_t v = d.test_idx[q];
-        if (v < 0 || v >= d.dims[q % d.order]) return s->fail(NTC_ERR_INDEX, "a held-out index is out of range");
+        if (v < 0 || v >= d.dims[q % d.order]) return j.admit_err = "a held-out index is out of range", NTC_ERR_INDEX;
     }
+    const size_t snap_bytes = sizeof(float) * (size_t)ntc::snapshot_floats(j.h);
     e = j.tidx.ensure(sizeof(int32_t) * (size_t)(d.n_test * d.order));
     if (e == cudaSuccess) e = j.tval.ensure(sizeof(float) * (size_t)d.n_test);
     if (e == cudaSuccess) e = j.scratch.ensure(sizeof(double) * ntc::kRmseScratch);
+    if (e == cudaSuccess) e = j.snap[0].ensure(snap_bytes);
+    if (e == cudaSuccess) e = j.snap[1].ensure(snap_bytes);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(j.tidx.p, d.test_idx, sizeof(int32_t) * (size_t)(d.n_test * d.order),
                             cudaMemcpyHostToDevice, j.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(j.tval.p, d.test_vals, sizeof(float) * (size_t)d.n_test, cudaMemcpyHostToDevice, j.stream);
+    if (e == cudaSuccess) e = ntc::snapshot_factors(j.h, j.snap[0].as<float>());
     if (e == cudaSuccess)
         e = ntc::rmse_enqueue(j.h, j.tidx.as<int32_t>(), j.tval.as<float>(), d.n_test, j.scratch.as<double>(),
                               j.host_sum);
     if (e == cudaSuccess) e = cudaStreamSynchronize(j.stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "job admission");
+    if (e != cudaSuccess) return cuda_err(e, "job admission");
     j.info.rmse0 = j.info.rmse = std::sqrt(*j.host_sum / (double)d.n_test);
     return NTC_OK;
 }
@@ -195,8 +252,12 @@ ntc_status admit_job(ntc_server* s, Job& j) {
 ntc_status enqueue_epoch(ntc_server* s, Job& j) {
     ntc_status r = ntc_epoch(j.h, nullptr, j.d.c, j.d.seed + (uint64_t)j.info.epochs);
     if (r != NTC_OK) return s->fail(r, ntc_last_error(j.h));
-    cudaError_t e = ntc::rmse_enqueue(j.h, j.tidx.as<int32_t>(), j.tval.as<float>(), j.d.n_test,
-                                      j.scratch.as<double>(), j.host_sum);
+    // factors after this epoch (number epochs + 1) go to the snapshot that
+    // queries do not read until the epoch is collected
+    cudaError_t e = ntc::snapshot_factors(j.h, j.snap[(j.info.epochs + 1) % 2].as<float>());
+    if (e == cudaSuccess)
+        e = ntc::rmse_enqueue(j.h, j.tidx.as<int32_t>(), j.tval.as<float>(), j.d.n_test, j.scratch.as<double>(),
+                              j.host_sum);
     if (e == cudaSuccess) e = cudaEventRecord(j.done_ev, j.stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "epoch enqueue");
     j.busy = true;
@@ -228,7 +289,10 @@ ntc_status ntc_server_create(double hbm_budget, int max_running, ntc_server** ou
     s->max_running = max_running;
     s->t0 = std::chrono::steady_clock::now();
     if (cudaGetDevice(&s->device) != cudaSuccess) return NTC_ERR_CUDA;
-    if (cudaStreamCreateWithFlags(&s->qstream, cudaStreamNonBlocking) != cudaSuccess) return NTC_ERR_CUDA;
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return NTC_ERR_CUDA;
+    if (cudaStreamCreateWithPriority(&s->qstream, cudaStreamNonBlocking, greatest) != cudaSuccess)
+        return NTC_ERR_CUDA;
     *out = s.release();
     return NTC_OK;
 }
@@ -261,6 +325,23 @@ ntc_status ntc_server_submit(ntc_server* s, const ntc_job_desc* desc, int64_t* j
 ntc_status ntc_server_step(ntc_server* s, int64_t* running, int64_t* queued) {
     if (!s) return NTC_ERR_ARG;
     if (cudaSetDevice(s->device) != cudaSuccess) return s->fail(NTC_ERR_CUDA, "cudaSetDevice");
+    // 0. memory of finished jobs that is free again, admissions that finished
+    collect_reaped(s, false);
+    for (auto& jp : s->jobs) {
+        Job& j = *jp;
+        if (!j.admitting || j.admit_state.load(std::memory_order_acquire) < 2) continue;
+        j.admit_thread.join();
+        if (j.admit_state.load() == 3) {
+            fail_job(s, j, j.admit_err);
+            continue;
+        }
+        j.admitting = false;
+        j.info.state = NTC_JOB_RUNNING;
+        if (!(j.info.rmse > j.d.target_rmse)) {   // already at the target
+            ntc_status r2 = finish_job(s, j, true);
+            if (r2 != NTC_OK) return r2;
+        }
+    }
     // 1. finished epochs
     for (auto& jp : s->jobs) {
         Job& j = *jp;
@@ -290,22 +371,20 @@ ntc_status ntc_server_step(ntc_server* s, int64_t* running, int64_t* queued) {
         if ((double)(s->st.bytes_in_use + j.info.bytes) > s->budget) break;
         s->queue.pop_front();
         s->st.queued -= 1;
-        ntc_status r = admit_job(s, j);
-        if (r != NTC_OK) {
-            const std::string why = s->err;
-            fail_job(s, j, why);
-            continue;
-        }
-        j.info.state = NTC_JOB_RUNNING;
+        // the memory is the job's from now on; upload and bucketing run aside
+        j.admitting = true;
         j.info.t_admit = s->now();
         s->st.running += 1;
         s->st.bytes_in_use += j.info.bytes;
         s->st.peak_bytes = std::max(s->st.peak_bytes, s->st.bytes_in_use);
         s->st.peak_running = std::max(s->st.peak_running, s->st.running);
-        if (!(j.info.rmse > j.d.target_rmse)) {   // already at the target
-            ntc_status r2 = finish_job(s, j, true);
-            if (r2 != NTC_OK) return r2;
-        }
+        j.admit_state.store(1);
+        Job* jp = &j;
+        const int dev = s->device;
+        j.admit_thread = std::thread([jp, dev] {
+            jp->admit_status = admit_job(*jp, dev);
+            jp->admit_state.store(jp->admit_status == NTC_OK ? 2 : 3, std::memory_order_release);
+        });
     }
     // 3. next epoch of every idle running job
     for (auto& jp : s->jobs) {
@@ -325,6 +404,8 @@ ntc_status ntc_server_step(ntc_server* s, int64_t* running, int64_t* queued) {
 
 ntc_status ntc_server_sync(ntc_server* s) {
     if (!s) return NTC_ERR_ARG;
+    for (auto& jp : s->jobs)   // admissions in progress: wait for their threads (a tick takes them over)
+        while (jp->admitting && jp->admit_state.load(std::memory_order_acquire) == 1) std::this_thread::yield();
     for (auto& jp : s->jobs)
         if (jp->info.state == NTC_JOB_RUNNING && jp->stream) {
             const cudaError_t e = cudaStreamSynchronize(jp->stream);
@@ -348,6 +429,7 @@ ntc_status ntc_server_predict(ntc_server* s, int64_t n, const int64_t* job_ids, 
     // the running jobs named by the queries, each once, in first-use order
     std::vector<int32_t> slot((size_t)n);
     std::vector<ntc_handle*> hs;
+    std::vector<const float*> snaps;
     std::vector<int64_t> slot_of(s->jobs.size(), -1);
     for (int64_t q = 0; q < n; ++q) {
         Job* j = find_job(s, job_ids[q]);
@@ -361,9 +443,9 @@ ntc_status ntc_server_predict(ntc_server* s, int64_t n, const int64_t* job_ids, 
         if (sl < 0) {
             sl = (int64_t)hs.size();
             hs.push_back(j->h);
-            // the query reads the factors after the job's enqueued epoch
-            const cudaError_t e = cudaStreamWaitEvent(s->qstream, j->done_ev, 0);
-            if (e != cudaSuccess) return cuda_fail(s, e, "query wait");
+            // factors after the last collected epoch; the epoch in flight
+            // writes the other snapshot
+            snaps.push_back(j->snap[j->info.epochs % 2].as<float>());
         }
         slot[(size_t)q] = (int32_t)sl;
     }
@@ -377,8 +459,8 @@ ntc_status ntc_server_predict(ntc_server* s, int64_t n, const int64_t* job_ids, 
         e = cudaMemcpyAsync(s->q_idx.p, idx, sizeof(int32_t) * (size_t)n * ntc::kMaxOrder, cudaMemcpyHostToDevice,
                             s->qstream);
     if (e == cudaSuccess)
-        e = ntc::predict_multi(hs.data(), (int)hs.size(), s->q_slot.as<int32_t>(), s->q_idx.as<int32_t>(), n,
-                               s->q_out.as<float>(), s->q_table.p, s->qstream);
+        e = ntc::predict_multi(hs.data(), snaps.data(), (int)hs.size(), s->q_slot.as<int32_t>(),
+                               s->q_idx.as<int32_t>(), n, s->q_out.as<float>(), s->q_table.p, s->qstream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, s->q_out.p, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s->qstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->qstream);
@@ -393,8 +475,21 @@ ntc_status ntc_server_get_factor(ntc_server* s, int64_t job_id, int mode, float*
     Job* j = find_job(s, job_id);
     if (!j || !out || mode < 0 || mode >= (j ? j->d.order : 0)) return NTC_ERR_ARG;
     if (j->info.state == NTC_JOB_RUNNING) {
-        const ntc_status r = ntc_get_factor(j->h, mode, out);
-        if (r != NTC_OK) return s->fail(r, ntc_last_error(j->h));
+        // the snapshot queries read: factors after the last collected epoch
+        const ntc_handle* h = j->h;
+        const int64_t I = h->dims[mode];
+        const int R = h->rank, RP = h->rp;
+        int64_t off = 0;
+        for (int i = 0; i < mode; ++i) off += h->dims[i] * RP;
+        std::vector<float> tmp((size_t)(I * RP));
+        cudaError_t e = cudaMemcpyAsync(tmp.data(), j->snap[j->info.epochs % 2].as<float>() + off,
+                                        sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost, s->qstream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->qstream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "factor snapshot");
+        const std::vector<int32_t>& inv = h->inv_h[mode];   // caller row -> stored row
+        for (int64_t r = 0; r < I; ++r)
+            std::copy(tmp.begin() + (size_t)inv[(size_t)r] * RP, tmp.begin() + (size_t)inv[(size_t)r] * RP + R,
+                      out + r * R);
         return NTC_OK;
     }
     if (j->info.state != NTC_JOB_DONE) return s->fail(NTC_ERR_STATE, "the job has no factors yet");
@@ -412,10 +507,11 @@ const char* ntc_server_last_error(const ntc_server* s) { return s ? s->err.c_str
 
 void ntc_server_destroy(ntc_server* s) {
     if (!s) return;
-    for (auto& jp : s->jobs) {
-        if (jp->stream) cudaStreamSynchronize(jp->stream);
-        release_job(s, *jp);
-    }
+    for (auto& jp : s->jobs)
+        if (jp->admit_thread.joinable()) jp->admit_thread.join();
+    collect_reaped(s, true);
+    for (auto& jp : s->jobs) free_device(*jp);
+    cudaSetDevice(s->device);
     if (s->qstream) cudaStreamDestroy(s->qstream);
     delete s;
 }

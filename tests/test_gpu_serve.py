@@ -117,7 +117,9 @@ def test_multi_job_prediction_matches_each_jobs_model():
         srv.step()
         time.sleep(0.002)
     srv.sync()
+    srv.step()
     assert all(srv.job_info(j)["state"] == ntc.JOB_RUNNING for j in ids)
+    assert all(srv.job_info(j)["epochs"] >= 1 for j in ids)
     rng = np.random.default_rng(0)
     q_job, q_idx, want = [], [], []
     for k, (s, p) in enumerate(jobs):
