@@ -369,6 +369,7 @@ def run_serve(args):
     probs = [synth.serving_job(s, sigma=sigma, test_frac=0.01) for s in specs]
     t_gen = time.perf_counter() - t_gen
     srv = ntc.Server(args.serve_budget, 64)
+    srv.set_param("max_enqueue_per_step", 2)
     clocks = Clocks(0)
     clocks.start()
     t0 = srv.now()

@@ -90,6 +90,12 @@ ntc_status ntc_job_bytes(const ntc_job_desc* desc, int64_t* out);
  * max_running: at most this many jobs run at once (>= 1). */
 ntc_status ntc_server_create(double hbm_budget, int max_running, ntc_server** out);
 
+/* "max_enqueue_per_step": at most this many epochs are enqueued by one tick
+ * (default unlimited), the scan resuming where the previous tick stopped, so
+ * that a tick stays short and queries issued between ticks are served soon.
+ * NTC_ERR_ARG for an unknown key or a value out of range. */
+ntc_status ntc_server_set_param(ntc_server* s, const char* key, double value);
+
 /* Queues a job; *job_id is its id (0, 1, ... in submission order).
  * NTC_ERR_ARG for an invalid description or a job larger than the budget. */
 ntc_status ntc_server_submit(ntc_server* s, const ntc_job_desc* desc, int64_t* job_id);

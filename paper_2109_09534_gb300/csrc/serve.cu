@@ -114,6 +114,8 @@ struct ntc_server {
     cudaStream_t qstream = nullptr;   // prediction queries
     DevMem q_slot, q_idx, q_out, q_table;
     int device = 0;
+    int max_enqueue = 1 << 30;        // epochs enqueued per tick
+    size_t rr = 0;                    // round-robin start of the enqueue scan
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
     ntc_status fail(ntc_status s, const std::string& m) {
@@ -297,6 +299,17 @@ ntc_status ntc_server_create(double hbm_budget, int max_running, ntc_server** ou
     return NTC_OK;
 }
 
+ntc_status ntc_server_set_param(ntc_server* s, const char* key, double value) {
+    if (!s || !key) return NTC_ERR_ARG;
+    const std::string k(key);
+    if (k == "max_enqueue_per_step") {
+        if (!(value >= 1.0 && value <= 1e9)) return s->fail(NTC_ERR_ARG, "max_enqueue_per_step must be >= 1");
+        s->max_enqueue = (int)value;
+        return NTC_OK;
+    }
+    return s->fail(NTC_ERR_ARG, "unknown server parameter: " + k);
+}
+
 ntc_status ntc_server_submit(ntc_server* s, const ntc_job_desc* desc, int64_t* job_id) {
     if (!s || !job_id) return NTC_ERR_ARG;
     std::string why;
@@ -386,9 +399,12 @@ ntc_status ntc_server_step(ntc_server* s, int64_t* running, int64_t* queued) {
             jp->admit_state.store(jp->admit_status == NTC_OK ? 2 : 3, std::memory_order_release);
         });
     }
-    // 3. next epoch of every idle running job
-    for (auto& jp : s->jobs) {
-        Job& j = *jp;
+    // 3. next epoch of idle running jobs, at most max_enqueue per tick, the
+    // scan starting where the last tick stopped
+    int enq = 0;
+    const size_t nj = s->jobs.size();
+    for (size_t k = 0; k < nj && enq < s->max_enqueue; ++k) {
+        Job& j = *s->jobs[(s->rr + k) % nj];
         if (j.info.state != NTC_JOB_RUNNING || j.busy) continue;
         ntc_status r = enqueue_epoch(s, j);
         if (r != NTC_OK) {
@@ -396,6 +412,8 @@ ntc_status ntc_server_step(ntc_server* s, int64_t* running, int64_t* queued) {
             fail_job(s, j, why);
             return r;
         }
+        ++enq;
+        s->rr = (s->rr + k + 1) % nj;
     }
     if (running) *running = s->st.running;
     if (queued) *queued = s->st.queued;

@@ -112,6 +112,7 @@ def load(path: Optional[str] = None):
         "ntc_job_bytes": [ctypes.POINTER(ntc_job_desc), ctypes.POINTER(i64)],
         "ntc_server_create": [dbl, i32, ctypes.POINTER(P)],
         "ntc_server_submit": [P, ctypes.POINTER(ntc_job_desc), ctypes.POINTER(i64)],
+        "ntc_server_set_param": [P, ctypes.c_char_p, dbl],
         "ntc_server_step": [P, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "ntc_server_sync": [P],
         "ntc_server_job_info": [P, i64, ctypes.POINTER(ntc_job_info)],
@@ -341,6 +342,9 @@ class Server:
 
     def __del__(self):
         self.close()
+
+    def set_param(self, key: str, value: float) -> None:
+        self._check(load().ntc_server_set_param(self._s, key.encode(), float(value)))
 
     def submit(self, dims, rank, lam, c, idx, vals, test_idx, test_vals, target_rmse, max_epochs,
                arrival=0.0, seed=1, init_seed=3, storage_bf16=0) -> int:

@@ -50,6 +50,7 @@ def test_each_job_alone_equals_the_mix():
     torch = require_gpu()
     jobs = small_jobs()
     mixed = ntc.Server(64e9, 8)
+    mixed.set_param("max_enqueue_per_step", 1)       # epochs of different jobs interleave tick by tick
     ids = [submit(mixed, k, s, p) for k, (s, p) in enumerate(jobs)]
     drain(mixed, ids)
     st = mixed.stats()
@@ -98,6 +99,11 @@ def test_a_job_is_not_admitted_before_it_arrives():
     require_gpu()
     s, p = small_jobs()[0]
     srv = ntc.Server(64e9, 8)
+    with pytest.raises(ntc.NTCError) as e:
+        srv.set_param("no_such_parameter", 1)
+    assert e.value.status == ntc.NTC_ERR_ARG
+    with pytest.raises(ntc.NTCError):
+        srv.set_param("max_enqueue_per_step", 0)
     t_arr = srv.now() + 0.4
     jid = submit(srv, 0, s, p, max_epochs=1, arrival=t_arr)
     srv.step()
