@@ -38,7 +38,7 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv;
         cudaStream_t ls = fork ? L.h->side : s;
         e = L.run_on(ls, NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
-            k_light<RP, EW, BF, NOR><<<p.n_light, kThreads, LightSmem<RP, EW, BF, NOR>::bytes(a.n_other), ls>>>(a);
+            k_light<RP, EW, BF, NOR><<<p.n_light, kLightThreads, LightSmem<RP, EW, BF, NOR>::bytes(a.n_other), ls>>>(a);
         });
         if (e != cudaSuccess) return e;
         if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;

@@ -18,16 +18,16 @@ namespace ntc {
 // This is how "the k_p positions with the smallest (key, position)" of the
 // sampling rule (Sec. II-B, Alg. 1 line 5) are found without a sort.
 // `hist` holds 256 + 8 unsigned ints of shared memory.
-template <class Get>
+template <int NTH = kThreads, class Get>
 __device__ unsigned long long block_select_kth(const Get& get, int n, int k, unsigned* hist) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long prefix = 0ull;
     int remaining = k;
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 56 - 8 * pass;
-        for (int i = tid; i < 256; i += kThreads) hist[i] = 0u;
+        for (int i = tid; i < 256; i += NTH) hist[i] = 0u;
         __syncthreads();
-        for (int j = tid; j < n; j += kThreads) {
+        for (int j = tid; j < n; j += NTH) {
             const unsigned long long c = get(j);
             // ~0 marks an unused slot; it is larger than every item, so
             // leaving it out cannot change the k-th smallest (k <= items)
@@ -92,21 +92,21 @@ __device__ unsigned long long block_select_kth(const Get& get, int n, int k, uns
 constexpr int kSelBins = 4096;
 constexpr int kSelCap = 512;
 
-template <class Get, class Digit, class BinMax>
+template <int NTH = kThreads, class Get, class Digit, class BinMax>
 __device__ unsigned long long block_select_digit(const Get& get, int n, int m, const Digit& digit,
                                                  const BinMax& binmax, unsigned* hist,
                                                  unsigned long long* mem, int* scan_tmp) {
-    constexpr int PER = kSelBins / kThreads;
-    static_assert(PER * kThreads == kSelBins && PER % 4 == 0, "bins per thread");
+    constexpr int PER = kSelBins / NTH;
+    static_assert(PER * NTH == kSelBins && PER % 4 == 0, "bins per thread");
     const int tid = threadIdx.x;
-    for (int i = tid; i < kSelBins / 4; i += kThreads) reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kSelBins / 4; i += NTH) reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) hist[kSelBins + 3] = 0u;
     __syncthreads();
-    for (int base = 0; base < n; base += kThreads * 8) {
+    for (int base = 0; base < n; base += NTH * 8) {
         unsigned long long c[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int j = base + u * kThreads + tid;
+            const int j = base + u * NTH + tid;
             c[u] = j < n ? get(j) : ~0ull;
         }
 #pragma unroll
@@ -126,7 +126,7 @@ __device__ unsigned long long block_select_digit(const Get& get, int n, int m, c
         own += (int)(v.x + v.y + v.z + v.w);
     }
     int total;
-    const int excl = block_exclusive_scan(own, scan_tmp, &total);
+    const int excl = block_exclusive_scan<NTH>(own, scan_tmp, &total);
     if (excl < m && m <= excl + own) {
         int cum = excl;
 #pragma unroll
@@ -146,13 +146,13 @@ __device__ unsigned long long block_select_digit(const Get& get, int n, int m, c
     if (need == cnt) return binmax(b);
     if (cnt > kSelCap) {
         __syncthreads();
-        return block_select_kth(get, n, m, hist);
+        return block_select_kth<NTH>(get, n, m, hist);
     }
-    for (int base = 0; base < n; base += kThreads * 8) {
+    for (int base = 0; base < n; base += NTH * 8) {
         unsigned long long c[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int j = base + u * kThreads + tid;
+            const int j = base + u * NTH + tid;
             c[u] = j < n ? get(j) : ~0ull;
         }
 #pragma unroll
@@ -161,7 +161,7 @@ __device__ unsigned long long block_select_digit(const Get& get, int n, int m, c
     }
     __syncthreads();
     unsigned long long* res = reinterpret_cast<unsigned long long*>(hist + kSelBins + 4);   // 8-byte aligned
-    for (int t = tid; t < cnt; t += kThreads) {
+    for (int t = tid; t < cnt; t += NTH) {
         const unsigned long long ct = mem[t];
         int r = 0;
         for (int u = 0; u < cnt; ++u) r += mem[u] < ct ? 1 : 0;
@@ -757,9 +757,13 @@ __device__ __forceinline__ void build_H_warp(const float* sum, float* H, float* 
 // shared memory, exact k-subset selection, Gram/data reduction, row update.
 // Shared memory: [visit list u16 x kLightMax | union(keys, Gram pipeline,
 // reduction)] + reduced sums, H, b, vectors, histogram.
+// Threads per light-row block: 128, so that 4 blocks (rows) share an SM and a
+// block barrier waits for 4 warps.
+constexpr int kLightThreads = 128;
+
 template <int RP, int EW, bool BF16, int NOR>
 struct LightSmem {
-    using G = Gram<RP, EW, BF16, kThreads, 0, NOR, 24>;
+    using G = Gram<RP, EW, BF16, kLightThreads, 0, NOR, 24>;
     static constexpr size_t VIS = kLightMax * 2;
     // keys, then the select's histogram and boundary-bin members
     static constexpr size_t KEYS = kLightMax * 4;
@@ -767,13 +771,14 @@ struct LightSmem {
     __host__ __device__ static constexpr size_t union_bytes(int no) {
         return G::region_bytes(no) > SEL ? G::region_bytes(no) : SEL;
     }
-    static constexpr size_t TAIL = (size_t)(kThreads / 32 + 16) * 4;
+    static constexpr size_t TAIL = (size_t)(kLightThreads / 32 + 16) * 4;
     __host__ __device__ static constexpr size_t bytes(int no) { return VIS + union_bytes(no) + TAIL; }
 };
 
 template <int RP, int EW, bool BF16, int NOR>
-__global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
-    using G = Gram<RP, EW, BF16, kThreads, 0, NOR, 24>;
+__global__ void __launch_bounds__(kLightThreads, 4) k_light(ModeArgs a) {
+    constexpr int LT = kLightThreads;
+    using G = Gram<RP, EW, BF16, LT, 0, NOR, 24>;
     using S = LightSmem<RP, EW, BF16, NOR>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int no = a.n_other;
@@ -795,7 +800,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
     unsigned long long T = ~0ull;
     if (k < n) {
         const KeyGen kg(a.ss);
-        for (int j = threadIdx.x; j < n; j += kThreads) keys[j] = kg.key(uq0 + j);
+        for (int j = threadIdx.x; j < n; j += LT) keys[j] = kg.key(uq0 + j);
         __syncthreads();
         auto get = [&](int j) -> unsigned long long {
             return ((unsigned long long)keys[j] << 32) | (unsigned long long)(uq0 + j);
@@ -805,11 +810,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
         auto binmax = [](unsigned b) -> unsigned long long {
             return ((unsigned long long)b << 52) | ((1ull << 52) - 1ull);
         };
-        T = block_select_digit(get, n, k, digit, binmax, hist, mem, scan_tmp);
+        T = block_select_digit<LT>(get, n, k, digit, binmax, hist, mem, scan_tmp);
     }
     // compaction in position order: warp w owns positions [w*seg, (w+1)*seg)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int seg = ((n + kThreads - 1) / kThreads) * 32;
+    const int seg = ((n + LT - 1) / LT) * 32;
     const int wb = warp * seg, we = min(n, wb + seg);
     auto chosen = [&](int j) -> bool {
         return j < we && (k == n || ((((unsigned long long)keys[j] << 32) | (uq0 + j)) <= T));
@@ -819,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
     if (lane == 0) scan_tmp[warp] = wcnt;
     __syncthreads();
     int off = 0, nsel = 0;
-    for (int w = 0; w < kThreads / 32; ++w) {
+    for (int w = 0; w < LT / 32; ++w) {
         const int c = scan_tmp[w];
         off += w < warp ? c : 0;
         nsel += c;
@@ -832,7 +837,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_light(ModeArgs a) {
     }
     __syncthreads();
     if (a.mask_out) {
-        for (int i = threadIdx.x; i < nsel; i += kThreads) a.mask_out[q0 + vis[i]] = 1;
+        for (int i = threadIdx.x; i < nsel; i += LT) a.mask_out[q0 + vis[i]] = 1;
         return;
     }
     G gr;

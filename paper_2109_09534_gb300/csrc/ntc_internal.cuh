@@ -122,9 +122,10 @@ __device__ __forceinline__ uint16_t f32_to_bf16_rne(float f) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
 
-// ---- block-wide exclusive scan of one int per thread (kThreads threads).
-// `tmp` holds kThreads/32 + 1 ints.  Returns the exclusive prefix; *total gets
+// ---- block-wide exclusive scan of one int per thread (NTH threads, a
+// multiple of 32 up to 1024).  `tmp` holds NTH/32 + 1 ints.  Returns the exclusive prefix; *total gets
 // the block sum.  Contains __syncthreads.
+template <int NTH = kThreads>
 __device__ __forceinline__ int block_exclusive_scan(int v, int* tmp, int* total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int x = v;
@@ -136,18 +137,18 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* tmp, int* total)
     if (lane == 31) tmp[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        int w = lane < kThreads / 32 ? tmp[lane] : 0;
+        int w = lane < NTH / 32 ? tmp[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
-        if (lane < kThreads / 32) tmp[lane] = w;   // inclusive warp prefix
-        if (lane == kThreads / 32 - 1) tmp[kThreads / 32] = w;
+        if (lane < NTH / 32) tmp[lane] = w;   // inclusive warp prefix
+        if (lane == NTH / 32 - 1) tmp[NTH / 32] = w;
     }
     __syncthreads();
     const int before = warp > 0 ? tmp[warp - 1] : 0;
-    *total = tmp[kThreads / 32];
+    *total = tmp[NTH / 32];
     const int r = before + x - v;
     __syncthreads();
     return r;
