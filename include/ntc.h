@@ -65,6 +65,10 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
  *                    copy (round-to-nearest-even of the float32 master)
  *   "init_seed"      seed of the initial factors drawn at ntc_set_observed (default 3)
  *   "keep_perm"      1: keep the bucket permutation for ntc_get_bucket (default 0)
+ *   "cache_staging"  1: keep ntc_set_observed's staging copy of the observations
+ *                    and its sort buffers (about nnz*(4N+20) bytes) for the next
+ *                    call instead of allocating and freeing them each time
+ *                    (default 1)
  *   "bracket_z"      width, in standard deviations, of the sampler's key bracket
  *                    (default 7; 0 forces the exact fallback selector)
  *   "heavy_rows"     rows with more than this many observations are split over

@@ -166,10 +166,33 @@ __global__ void k_row_ptr(const uint32_t* keys, int64_t n, int64_t dim, int64_t*
     }
 }
 
-// Observations per row of `mode` (exact integer histogram).
-__global__ void k_count_rows(const int32_t* idx, int64_t n, int order, int mode, uint32_t* counts) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&counts[idx[e * order + mode]], 1u);
+// Observations per row of `mode` (exact integer histogram).  Skewed indices
+// put a large share of all increments on a few rows, so increments are first
+// combined: in a block-private shared-memory histogram when the mode has at
+// most kCountSmemRows rows (flushed once per block), else among the lanes of a
+// warp that hold the same row.
+constexpr int kCountSmemRows = 12288;
+__global__ void __launch_bounds__(256) k_count_rows(const int32_t* idx, int64_t n, int order, int mode, int64_t rows,
+                                                    uint32_t* counts) {
+    __shared__ uint32_t sh[kCountSmemRows];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (rows <= kCountSmemRows) {
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) sh[i] = 0u;
+        __syncthreads();
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride)
+            atomicAdd(&sh[idx[e * order + mode]], 1u);
+        __syncthreads();
+        for (int i = threadIdx.x; i < rows; i += blockDim.x)
+            if (sh[i]) atomicAdd(&counts[i], sh[i]);
+        return;
+    }
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x; e0 < n; e0 += stride) {
+        const int64_t e = e0 + threadIdx.x;
+        const bool in = e < n;
+        const int r = in ? idx[e * order + mode] : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, r);
+        if (in && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&counts[r], (unsigned)__popc(same));
+    }
 }
 
 struct RowMaps {

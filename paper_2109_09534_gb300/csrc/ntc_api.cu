@@ -373,7 +373,8 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
     cudaStream_t s = h->stream;
     const int N = h->order;
     // stage and validate before touching the handle's current data
-    DevMem cidx, cval;
+    DevMem& cidx = h->stage_idx;
+    DevMem& cval = h->stage_val;
     NTC_CUDA(h, cidx.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz * N, 1)));
     NTC_CUDA(h, cval.ensure(sizeof(float) * (size_t)std::max<int64_t>(nnz, 1)));
     if (nnz > 0) {
@@ -381,7 +382,7 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
         NTC_CUDA(h, cudaMemcpyAsync(cidx.p, idx, sizeof(int32_t) * nnz * N, kind, s));
         NTC_CUDA(h, cudaMemcpyAsync(cval.p, vals, sizeof(float) * nnz, kind, s));
     }
-    DevMem bad;
+    DevMem& bad = h->bad_flag;
     NTC_CUDA(h, bad.ensure(sizeof(unsigned)));
     NTC_CUDA(h, cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
     if (nnz > 0) k_validate<<<grid_for(nnz), 256, 0, s>>>(cidx.as<int32_t>(), nnz, N, h->dims_dev.as<int64_t>(),
@@ -390,7 +391,7 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
     NTC_CUDA(h, cudaMemcpyAsync(&bad_h, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     NTC_CUDA(h, cudaStreamSynchronize(s));
     if (bad_h) return fail(h, NTC_ERR_INDEX, "an observed index is out of range");
-    // commit
+    // commit (the previous COO becomes the next call's staging buffer)
     std::swap(h->coo_idx.p, cidx.p);
     std::swap(h->coo_idx.bytes, cidx.bytes);
     std::swap(h->coo_val.p, cval.p);
@@ -409,10 +410,13 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
     // observation counts per row -> storage order (most frequent first, ties by row)
     for (int i = 0; i < N; ++i) {
         const int64_t I = h->dims[i];
-        DevMem cnt;
+        DevMem& cnt = h->row_cnt;
         NTC_CUDA(h, cnt.ensure(sizeof(uint32_t) * (size_t)I));
         NTC_CUDA(h, cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t) * (size_t)I, s));
-        if (nnz > 0) k_count_rows<<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), nnz, N, i, cnt.as<uint32_t>());
+        // (few blocks when each flushes a shared histogram of the whole mode)
+        const int cgrid = I <= kCountSmemRows ? grid_for(nnz, 256, 152 * 2) : grid_for(nnz);
+        if (nnz > 0)
+            k_count_rows<<<cgrid, 256, 0, s>>>(h->coo_idx.as<int32_t>(), nnz, N, i, I, cnt.as<uint32_t>());
         NTC_CUDA(h, cudaGetLastError());
         std::vector<uint32_t> c((size_t)I);
         NTC_CUDA(h, cudaMemcpyAsync(c.data(), cnt.p, sizeof(uint32_t) * (size_t)I, cudaMemcpyDeviceToHost, s));
@@ -429,7 +433,8 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
     RowMaps maps;
     for (int i = 0; i < N; ++i) maps.inv[i] = h->inv_dev[i].as<int32_t>();
     // per-mode buckets
-    DevMem k0, k1, v0, v1, hist, sums;
+    DevMem &k0 = h->sort_k0, &k1 = h->sort_k1, &v0 = h->sort_v0, &v1 = h->sort_v1, &hist = h->sort_hist,
+           &sums = h->sort_sums;
     const size_t nb4 = sizeof(uint32_t) * (size_t)std::max<int64_t>(nnz, 1);
     NTC_CUDA(h, k0.ensure(nb4));
     NTC_CUDA(h, k1.ensure(nb4));
@@ -484,7 +489,12 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
             h->rows_dev[i].as<int32_t>());
     }
     NTC_CUDA(h, cudaGetLastError());
-    NTC_CUDA(h, cudaStreamSynchronize(s));   // temporaries are freed on return
+    NTC_CUDA(h, cudaStreamSynchronize(s));
+    if (!h->cache_staging) {
+        for (DevMem* m : {&h->stage_idx, &h->stage_val, &h->sort_k0, &h->sort_k1, &h->sort_v0, &h->sort_v1,
+                          &h->sort_hist, &h->sort_sums, &h->row_cnt})
+            m->release();
+    }
     return NTC_OK;
 }
 
@@ -575,7 +585,9 @@ int64_t handle_device_bytes(const ntc_handle* h) {
     b += (int64_t)(h->Y.bytes + h->coo_idx.bytes + h->coo_val.bytes + h->dims_dev.bytes + h->vis.bytes +
                    h->vis_cnt.bytes + h->cand.bytes + h->cand_cnt.bytes + h->extra.bytes + h->extra_cnt.bytes +
                    h->flags.bytes + h->partial.bytes + h->partial2.bytes + h->row_sum.bytes + h->stat.bytes +
-                   h->red.bytes + h->mask.bytes);
+                   h->red.bytes + h->mask.bytes + h->stage_idx.bytes + h->stage_val.bytes + h->sort_k0.bytes +
+                   h->sort_k1.bytes + h->sort_v0.bytes + h->sort_v1.bytes + h->sort_hist.bytes + h->sort_sums.bytes +
+                   h->bad_flag.bytes + h->row_cnt.bytes);
     return b;
 }
 
@@ -689,6 +701,8 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
         h->profile = v != 0.0;
     } else if (k == "keep_perm") {
         h->keep_perm = v != 0.0;
+    } else if (k == "cache_staging") {
+        h->cache_staging = v != 0.0 ? 1 : 0;
     } else if (k == "bracket_z") {
         if (!(v >= 0 && v <= 1e6)) return fail(h, NTC_ERR_ARG, "bracket_z must be in [0, 1e6]");
         h->bracket_z = v;

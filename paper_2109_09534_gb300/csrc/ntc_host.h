@@ -95,6 +95,10 @@ struct ntc_handle {
     // scratch
     ntc::DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, partial2, row_sum, stat, red,
         mask;
+    // ntc_set_observed staging (the next COO) and radix-sort buffers, kept
+    // between calls unless "cache_staging" is 0
+    int cache_staging = 1;
+    ntc::DevMem stage_idx, stage_val, sort_k0, sort_k1, sort_v0, sort_v1, sort_hist, sort_sums, bad_flag, row_cnt;
     // per-kernel event timing ("profile")
     int profile = 0;
     struct Pending {

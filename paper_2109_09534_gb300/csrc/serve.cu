@@ -224,6 +224,7 @@ ntc_status admit_job(Job& j, int device) {
     };
     if (!chk(ntc_set_stream(j.h, j.stream)) || !chk(ntc_set_param(j.h, "storage_bf16", d.storage_bf16 ? 1.0 : 0.0)) ||
         !chk(ntc_set_param(j.h, "init_seed", (double)d.init_seed)) ||
+        !chk(ntc_set_param(j.h, "cache_staging", 0.0)) ||
         !chk(ntc_set_observed(j.h, d.nnz, d.idx, d.vals)) || !chk(ntc::prepare_epoch(j.h, d.c)))
         return r;
     for (int64_t q = 0; q < d.n_test * d.order; ++q) {
