@@ -52,13 +52,20 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* keys, i
 
 // Stable scatter: warp w of a tile owns keys [w*512, w*512+512) in order, in
 // 16 rounds of 32; equal digits within a round are ranked by lane, rounds and
-// warps in order, so the output keeps the input order of equal keys.
+// warps in order, so the output keeps the input order of equal keys.  The tile
+// is first placed in shared memory in (digit, input order) order and then
+// written out front to back, so that the global writes of one digit's run are
+// contiguous.
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* kin, const uint32_t* vin,
                                                             uint32_t* kout, uint32_t* vout, int64_t n,
                                                             int shift, const uint32_t* offs, int ntiles) {
     __shared__ unsigned wh[kThreads / 32][256];
+    __shared__ uint32_t sk[kSortTile], sv[kSortTile];
+    __shared__ int gbase[256];   // global position of a digit's run minus its tile-local start
+    __shared__ int scan_tmp[kThreads / 32 + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortIPT);
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + (int64_t)warp * (32 * kSortIPT);
     uint32_t key[kSortIPT], val[kSortIPT];
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) {
@@ -79,8 +86,14 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* kin,
     }
     __syncthreads();
     {
+        // thread d: the digit's tile-local start, then per-warp starts
         const int d = threadIdx.x;
-        unsigned run = offs[(int64_t)d * ntiles + blockIdx.x];
+        int cnt = 0;
+        for (int w = 0; w < kThreads / 32; ++w) cnt += (int)wh[w][d];
+        int tot;
+        const int start = block_exclusive_scan(cnt, scan_tmp, &tot);
+        gbase[d] = (int)offs[(int64_t)d * ntiles + blockIdx.x] - start;
+        unsigned run = (unsigned)start;
         for (int w = 0; w < kThreads / 32; ++w) {
             const unsigned t = wh[w][d];
             wh[w][d] = run;
@@ -99,9 +112,17 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* kin,
         if (valid && (peers & lt) == 0) wh[warp][d] += __popc(peers);
         __syncwarp();
         if (valid) {
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            sk[pos] = key[r];
+            sv[pos] = val[r];
         }
+    }
+    __syncthreads();
+    const int tn = (int)min((int64_t)kSortTile, n - tile0);
+    for (int i = threadIdx.x; i < tn; i += kThreads) {
+        const uint32_t k = sk[i];
+        const int64_t g = (int64_t)gbase[(k >> shift) & 255u] + i;
+        kout[g] = k;
+        vout[g] = sv[i];
     }
 }
 
@@ -199,23 +220,30 @@ struct RowMaps {
     const int32_t* inv[kMaxOrder];   // original row -> storage row, per mode
 };
 
-// Bucket entries of `mode` in sorted order: the other modes' indices mapped
-// to their storage rows, then the value.
+// Bucket entries of `mode` (the other modes' indices mapped to their storage
+// rows, then the value) in input order, with coalesced reads of the COO;
+// k_gather_entries then puts them in bucket order with one random 16- or
+// 32-byte read per entry.
 template <int EW>
-__global__ void k_fill_bucket(const int32_t* idx, const float* vals, const uint32_t* perm, int64_t n,
-                              int order, int mode, RowMaps maps, Entry<EW>* out) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = perm[q];
+__global__ void k_build_entries(const int32_t* idx, const float* vals, int64_t n, int order, int mode, RowMaps maps,
+                                Entry<EW>* out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         Entry<EW> en;
+        // slot w holds mode w, or w + 1 past `mode` (slot positions fixed at compile time)
 #pragma unroll
-        for (int w = 0; w < EW; ++w) en.w[w] = 0;
-        int o = 0;
-        for (int i = 0; i < order; ++i)
-            if (i != mode) en.w[o++] = maps.inv[i][idx[e * order + i]];
+        for (int w = 0; w < EW - 1; ++w) {
+            const int src = w + (w >= mode ? 1 : 0);
+            en.w[w] = src < order ? maps.inv[src][idx[e * order + src]] : 0;
+        }
         en.w[EW - 1] = __float_as_int(vals[e]);
-        out[q] = en;
+        out[e] = en;
     }
+}
+
+template <int EW>
+__global__ void k_gather_entries(const Entry<EW>* in, const uint32_t* perm, int64_t n, Entry<EW>* out) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = in[perm[q]];
 }
 
 // Fixed-order double-precision sums: per-block partials, then one block.

@@ -452,12 +452,18 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
         k_row_ptr<<<grid_for(nnz + 1), 256, 0, s>>>(keys, nnz, h->dims[i], h->row_ptr[i].as<int64_t>());
         NTC_CUDA(h, h->bucket[i].ensure((size_t)EW * 4 * (size_t)std::max<int64_t>(nnz, 1)));
         if (nnz > 0) {
-            if (EW == 4)
-                k_fill_bucket<4><<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), perm,
-                                                               nnz, N, i, maps, h->bucket[i].as<Entry<4>>());
-            else
-                k_fill_bucket<8><<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), perm,
-                                                               nnz, N, i, maps, h->bucket[i].as<Entry<8>>());
+            NTC_CUDA(h, h->entry_tmp.ensure((size_t)EW * 4 * (size_t)nnz));
+            if (EW == 4) {
+                k_build_entries<4><<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), nnz,
+                                                                 N, i, maps, h->entry_tmp.as<Entry<4>>());
+                k_gather_entries<4><<<grid_for(nnz), 256, 0, s>>>(h->entry_tmp.as<Entry<4>>(), perm, nnz,
+                                                                  h->bucket[i].as<Entry<4>>());
+            } else {
+                k_build_entries<8><<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), nnz,
+                                                                 N, i, maps, h->entry_tmp.as<Entry<8>>());
+                k_gather_entries<8><<<grid_for(nnz), 256, 0, s>>>(h->entry_tmp.as<Entry<8>>(), perm, nnz,
+                                                                  h->bucket[i].as<Entry<8>>());
+            }
         }
         if (h->keep_perm) {
             NTC_CUDA(h, h->perm[i].ensure(nb4));
@@ -492,7 +498,7 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
     NTC_CUDA(h, cudaStreamSynchronize(s));
     if (!h->cache_staging) {
         for (DevMem* m : {&h->stage_idx, &h->stage_val, &h->sort_k0, &h->sort_k1, &h->sort_v0, &h->sort_v1,
-                          &h->sort_hist, &h->sort_sums, &h->row_cnt})
+                          &h->sort_hist, &h->sort_sums, &h->row_cnt, &h->entry_tmp})
             m->release();
     }
     return NTC_OK;
@@ -587,7 +593,7 @@ int64_t handle_device_bytes(const ntc_handle* h) {
                    h->flags.bytes + h->partial.bytes + h->partial2.bytes + h->row_sum.bytes + h->stat.bytes +
                    h->red.bytes + h->mask.bytes + h->stage_idx.bytes + h->stage_val.bytes + h->sort_k0.bytes +
                    h->sort_k1.bytes + h->sort_v0.bytes + h->sort_v1.bytes + h->sort_hist.bytes + h->sort_sums.bytes +
-                   h->bad_flag.bytes + h->row_cnt.bytes);
+                   h->bad_flag.bytes + h->row_cnt.bytes + h->entry_tmp.bytes);
     return b;
 }
 

@@ -97,6 +97,7 @@ int64_t model_bytes(const ntc_job_desc* d) {
     b += d->n_test * (4 * N + 4) + ntc::kRmseScratch * 8;    // held-out set
     b += 2 * sum_dims * rp * 4;                               // two factor snapshots for queries
     b += nnz * (4 * N + 4) + nnz * 16 + (nnz / 256 + 1) * 8;  // admission: COO copy + sort buffers
+    b += nnz * ent;                                           // admission: entries before the bucket gather
     b += 8 << 20;                                             // small buffers and allocation rounding
     return b;
 }
