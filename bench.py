@@ -184,6 +184,14 @@ def barrier(ws):
         td.barrier()
 
 
+def replica_value(units_per_rank, ws, ms_local):
+    """Whole-job throughput of ws independent replicas (weak scaling): the
+    units all ranks processed over the slowest rank's time.  Returns (value
+    per second, max ms)."""
+    ms = max_over_ranks(ms_local, ws)
+    return ws * units_per_rank / (ms * 1e-3), ms
+
+
 def cpu_baseline(p, steps=1, warmup=0):
     """The FP64 oracle as it stands, OpenMP over rows (the paper's Algorithm 3),
     on the host cores.  Bounded sample: one call of Algorithm 1 on mode 0 of the
@@ -275,11 +283,10 @@ def run_ntc(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier(ws)
-    ms = max_over_ranks(ev0.elapsed_time(ev1), ws)
+    value, ms = replica_value(p.nnz * args.steps, ws, ev0.elapsed_time(ev1))
     prof = g.profile()
 
     ms_step = ms / args.steps
-    value = ws * p.nnz * args.steps / (ms * 1e-3)
     hbm, hbm_kind = peaks()
     # dominant kernel and its roofline
     # (kernels that carry algorithmic bytes: the sampler and resolver touch
