@@ -72,7 +72,14 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     std::vector<int2> heavy_groups;
     std::vector<longlong2> brk;
     int64_t visits = 0, visits_heavy = 0, updated = 0, skipped = 0, cand_total = 0, extra_total = 0;
-    for (int64_t r = 0; r < P; ++r) {
+    // rows in descending order of observations (ties by row), so that the
+    // per-row blocks of the longest split rows start first
+    std::vector<int32_t> order((size_t)P);
+    for (int64_t r = 0; r < P; ++r) order[(size_t)r] = (int32_t)r;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return rp[(size_t)x + 1] - rp[(size_t)x] > rp[(size_t)y + 1] - rp[(size_t)y];
+    });
+    for (const int32_t r : order) {
         const int64_t n = rp[r + 1] - rp[r];
         const int64_t k = (int64_t)std::floor(c * (double)n);   // B_{l,p} = floor(c ||M(p,:)||_0)
         if (k == 0) {
