@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage-bf16", action="store_true")
+    ap.add_argument("--workload", default="zipf", choices=["zipf", "uber"],
+                    help="zipf: Zipf(1.1) 10^4-cube, R=32; uber: the Uber-shaped 4-way timing twin")
+    ap.add_argument("--rank", type=int, default=0, help="fitted rank (default: the workload's)")
     # serving stream (continuous-batching completion server)
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead of the epoch bench")
     ap.add_argument("--serve-full", action="store_true",
@@ -52,24 +55,38 @@ def parse():
     ap.add_argument("--serve-budget", type=float, default=150e9, help="HBM budget, bytes")
     ap.add_argument("--serve-max-epochs", type=int, default=40)
     ap.add_argument("--serve-qps", type=float, default=10000.0, help="prediction queries per second")
+    # convergence study (synthetic twin of the MovieLens experiments)
+    ap.add_argument("--study", default="", choices=["", "convergence"])
+    ap.add_argument("--study-trials", type=int, default=5)
+    ap.add_argument("--study-epochs", type=int, default=100)
+    ap.add_argument("--study-nnz", type=int, default=10_000_000)
     return ap.parse_args()
 
 
-def workload(nnz):
+def workload(args):
     from paper_2109_09534_gb300 import synth
-    return synth.zipf_1e4cube(nnz_total=nnz)
+    p = synth.uber_twin() if args.workload == "uber" else synth.zipf_1e4cube(nnz_total=args.nnz)
+    if args.rank:
+        p.rank = args.rank
+    return p
 
 
 def config(p, args):
-    return {
-        "workload": f"zipf1.1 10000^3 tensor, R=32, {args.nnz // 1_000_000}M draws "
-                    f"({p.nnz} train), c=0.1, MAX_INNER=1, "
-                    f"{'bf16' if args.storage_bf16 else 'fp32'} factor storage",
-        "dims": p.dims, "rank": p.rank, "nnz_train": p.nnz, "c": p.c, "lambda": p.lam,
-        "step": "one epoch = 10 AO iterations x 3 modes",
-        "l2": "inputs larger than L2: 3 per-mode buckets of 16 B/entry (~4.7 GB) re-read every epoch",
-        "parallelism": "replicas" if args.gpus > 1 else "single GPU",
-    }
+    import math
+    T = int(math.ceil(1.0 / p.c - 1e-12))
+    N = len(p.dims)
+    storage = "bf16" if args.storage_bf16 else "fp32"
+    if args.workload == "uber":
+        text = (f"uber-shaped 183x24x1140x1717 tensor, 3,309,490 uniform draws of a planted rank-10 "
+                f"noiseless tensor ({p.nnz} train), fitted R={p.rank}, c=0.5, MAX_INNER=1, {storage} factor storage")
+        l2 = "inputs larger than L2: 4 per-mode buckets of 16 B/entry (0.21 GB) re-read every epoch"
+    else:
+        text = (f"zipf1.1 10000^3 tensor, R={p.rank}, {args.nnz // 1_000_000}M draws ({p.nnz} train), c=0.1, "
+                f"MAX_INNER=1, {storage} factor storage")
+        l2 = "inputs larger than L2: 3 per-mode buckets of 16 B/entry (~4.7 GB) re-read every epoch"
+    return {"workload": text, "dims": p.dims, "rank": p.rank, "nnz_train": p.nnz, "c": p.c, "lambda": p.lam,
+            "step": f"one epoch = {T} AO iterations x {N} modes", "l2": l2,
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
 def peaks():
@@ -204,6 +221,18 @@ def cpu_baseline(p, steps=1, warmup=0):
     o = oracle.Oracle(p.dims, p.rank, p.lam, omp=True)
     o.set_observed(p.idx_train, p.val_train.astype(np.float64))
     o.init_factors(3)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = int(os.environ.get("OMP_NUM_THREADS", cores))
+    if p.nnz <= 10_000_000:   # small workload: whole epochs
+        times = []
+        for s in range(warmup + steps):
+            t0 = time.perf_counter()
+            o.epoch(p.c, seed=4 + s)
+            if s >= warmup:
+                times.append(time.perf_counter() - t0)
+        t_epoch = statistics.median(times)
+        return {"value": p.nnz / t_epoch, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"whole epochs of the {p.nnz}-entry workload, {t_epoch:.2f} s median of {steps}"}, times
     for w in range(warmup):
         o.ao_iter = 1000 + w
         o.snmc(0, p.c, seed=4)
@@ -213,19 +242,18 @@ def cpu_baseline(p, steps=1, warmup=0):
         t0 = time.perf_counter()
         o.snmc(0, p.c, seed=4)
         times.append(time.perf_counter() - t0)
-    t_epoch = statistics.median(times) * 3 * int(np.ceil(1.0 / p.c - 1e-12))
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": p.nnz / t_epoch, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
-            "kind": "oracle",
+    calls = len(p.dims) * int(np.ceil(1.0 / p.c - 1e-12))
+    t_epoch = statistics.median(times) * calls
+    return {"value": p.nnz / t_epoch, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one Algorithm-1 call (mode 0, c={p.c}) on the full {p.nnz}-entry workload, "
-                      f"{statistics.median(times):.2f} s median of {steps}; epoch = 30 such calls"}, times
+                      f"{statistics.median(times):.2f} s median of {steps}; epoch = {calls} such calls"}, times
 
 
 def run_reference(args):
     ws, rank, _ = dist()
     if rank != 0:
         return
-    p = workload(args.nnz)
+    p = workload(args)
     cb, times = cpu_baseline(p, steps=args.steps, warmup=args.warmup)
     v = cb["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -246,7 +274,7 @@ def run_ntc(args):
     torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
-    p = workload(args.nnz)
+    p = workload(args)
     params = dict(profile=1)
     if args.storage_bf16:
         params["storage_bf16"] = 1
@@ -301,7 +329,8 @@ def run_ntc(args):
     total_k = sum(v["ms"] for v in prof.values())
     R, N = p.rank, p.order
     flops_per_visit = (N - 2) * R + 2 * R + R * (R + 1)
-    gram_flops = prof["heavy_gram"]["alg_bytes"] // ((N - 1) * 4 + 4 + (N - 1) * R * 4) * flops_per_visit
+    s_bytes = 2 if args.storage_bf16 else 4
+    gram_flops = prof["heavy_gram"]["alg_bytes"] // ((N - 1) * 4 + 4 + (N - 1) * R * s_bytes) * flops_per_visit
     gram_tf = gram_flops / (prof["heavy_gram"]["ms"] * 1e-3) / 1e12 if prof["heavy_gram"]["ms"] > 0 else 0.0
 
     # end to end through the C ABI with pinned host buffers
@@ -444,8 +473,63 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_study(args):
+    """Convergence study: RRE of the held-out entries against the planted
+    (noise-free) values after each epoch, for minibatch fractions c and two
+    noise levels, over several seeded trials (Sec. IV-B experiments, on a
+    planted tensor of MovieLens-10M's shape instead of the dataset)."""
+    import numpy as np
+    import torch
+
+    from paper_2109_09534_gb300 import ntc, synth
+
+    dims, R = [71567, 65133, 730], 10
+    snrs_db = [40.0, 20.0]
+    cs = [0.05, 0.2, 0.5]
+    marks = [e for e in (1, 2, 5, 10, 20, 50, 100, 200) if e <= args.study_epochs]
+    stream = torch.cuda.current_stream().cuda_stream
+    res = {}
+    t0 = time.perf_counter()
+    for snr in snrs_db:
+        for trial in range(args.study_trials):
+            p0 = synth.make_problem(dims, R, args.study_nnz, lam=1e-3, c=0.1, index_dist="uniform", sigma=0.0,
+                                    test_frac=0.01, seed=100 + trial, name="ml10m-twin")
+            # noise for the requested SNR: sigma^2 = E[x^2] / 10^(snr/10)
+            power = float(np.mean(p0.val_train.astype(np.float64) ** 2))
+            sigma = float(np.sqrt(power / 10 ** (snr / 10)))
+            rng = np.random.default_rng(7000 + trial)
+            vals = (p0.val_train + sigma * rng.standard_normal(p0.val_train.shape)).astype(np.float32)
+            clean = p0.val_test_clean
+            for c in cs:
+                g = ntc.NTC(dims, R, p0.lam, stream=stream, init_seed=3 + trial)
+                g.set_observed(p0.idx_train, vals)
+                curve = {}
+                for e in range(1, args.study_epochs + 1):
+                    g.epoch(c, seed=10_000 * trial + e)
+                    if e in marks:
+                        x = g.predict(p0.idx_test).astype(np.float64)
+                        curve[e] = float(np.linalg.norm(x - clean) / np.linalg.norm(clean))
+                g.close()
+                res.setdefault((snr, c), []).append(curve)
+    table = {}
+    for (snr, c), curves in res.items():
+        key = f"snr{snr:g}dB_c{c:g}"
+        table[key] = {str(e): {"mean": float(np.mean([cv[e] for cv in curves])),
+                               "std": float(np.std([cv[e] for cv in curves]))} for e in marks}
+    line = {"metric": "held-out RRE vs epoch", "mode": "study", "unit": "relative", "data": "synthetic",
+            "config": {"workload": f"planted rank-{R} U[0,1] tensor of MovieLens-10M shape {dims}, "
+                                   f"{args.study_nnz} uniform draws (1% held out), lambda 1e-3, fitted R = {R}, "
+                                   f"SNR {snrs_db} dB, c {cs}, {args.study_trials} trials, "
+                                   f"{args.study_epochs} epochs"},
+            "rre": table, "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.study:
+        run_study(args)
+        return
     if args.serve:
         run_serve(args)
         return

@@ -234,3 +234,11 @@ def serving_job(spec: JobSpec, sigma: float = 0.01, test_frac: float = 0.01) -> 
     return make_problem(spec.dims, spec.rank, spec.nnz, lam=1e-3, c=0.1, index_dist="uniform",
                         sigma=sigma, test_frac=test_frac, seed=spec.data_seed,
                         name=f"job-{len(spec.dims)}way-R{spec.rank}-{spec.nnz}")
+
+
+def uber_twin(seed: int = 1) -> Problem:
+    """Uber-Pickups-shaped timing twin (Sec. IV-C): 183 x 24 x 1140 x 1717,
+    3,309,490 uniform draws of a planted rank-10 tensor with U[0,1] factors,
+    noiseless, c = 0.5, 2% held out.  The fitted rank is the caller's."""
+    return make_problem([183, 24, 1140, 1717], 10, 3_309_490, lam=1e-3, c=0.5, index_dist="uniform",
+                        sigma=0.0, test_frac=0.02, seed=seed, name="uber-twin-4way-planted-R10")
