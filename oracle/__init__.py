@@ -61,6 +61,8 @@ def _lib(omp: bool = False):
                                  ctypes.c_int64, P, P]
         L.orc_power_lmax.restype = ctypes.c_double
         L.orc_power_lmax.argtypes = [ctypes.c_int, P, ctypes.c_int]
+        L.orc_power_lmax_v.restype = ctypes.c_double
+        L.orc_power_lmax_v.argtypes = [ctypes.c_int, P, ctypes.c_int, P]
         L.orc_jacobi_lmax.restype = ctypes.c_double
         L.orc_jacobi_lmax.argtypes = [ctypes.c_int, P]
         L.orc_row_update.restype = ctypes.c_int64
@@ -144,6 +146,16 @@ def power_lmax(H: np.ndarray, iters: int = 10) -> float:
     """Power-method estimate of max eig(H) (Alg. 1 line 10, Sec. II-B item 4)."""
     H = np.ascontiguousarray(H, dtype=np.float64)
     return float(_lib().orc_power_lmax(H.shape[0], _ptr(H), iters))
+
+
+def power_lmax_v(H: np.ndarray, iters: int, v: np.ndarray = None):
+    """Power method from start vector v (None: ones/sqrt(R)); returns
+    (estimate, last normalised iterate)."""
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    R = H.shape[0]
+    vv = np.full(R, 1.0 / np.sqrt(R)) if v is None else np.array(v, dtype=np.float64)
+    mu = float(_lib().orc_power_lmax_v(R, _ptr(H), iters, _ptr(vv)))
+    return mu, vv
 
 
 def jacobi_lmax(H: np.ndarray) -> float:

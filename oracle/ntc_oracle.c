@@ -116,10 +116,16 @@ int orc_bucket(int order, int64_t nnz, const int32_t* idx, int mode, int64_t dim
 /* L_p = max eig(H_{l,p}) (Alg. 1 line 10) by the power method (Sec. II-B,
  * cost item 4): v0 = ones/sqrt(R); w = H v; mu = v'w; v = w/||w||. */
 double orc_power_lmax(int R, const double* H, int iters) {
+    return orc_power_lmax_v(R, H, iters, NULL);
+}
+
+/* The same from the start vector v_io (NULL: ones/sqrt(R)); on return v_io
+ * holds the last normalised iterate (the warm start of the next call). */
+double orc_power_lmax_v(int R, const double* H, int iters, double* v_io) {
     double* v = (double*)malloc(sizeof(double) * (size_t)R);
     double* w = (double*)malloc(sizeof(double) * (size_t)R);
     double mu = 0.0;
-    for (int r = 0; r < R; ++r) v[r] = 1.0 / sqrt((double)R);
+    for (int r = 0; r < R; ++r) v[r] = v_io ? v_io[r] : 1.0 / sqrt((double)R);
     for (int t = 0; t < iters; ++t) {
         for (int i = 0; i < R; ++i) {
             double acc = 0.0;
@@ -139,6 +145,8 @@ double orc_power_lmax(int R, const double* H, int iters) {
         double nrm = sqrt(ww);
         for (int i = 0; i < R; ++i) v[i] = w[i] / nrm;
     }
+    if (v_io)
+        for (int r = 0; r < R; ++r) v_io[r] = v[r];
     free(v);
     free(w);
     return mu;
@@ -193,6 +201,7 @@ struct orc_state {
     double lambda;
     int max_inner;
     int power_iters;
+    int power_warm;     /* 1: each row's power method starts from its last vector */
     int lp_exact;
     int debug;
     uint64_t ao_iter;
@@ -202,6 +211,7 @@ struct orc_state {
     double* U[ORC_MAX_ORDER];
     int64_t* row_ptr[ORC_MAX_ORDER];
     int64_t* perm[ORC_MAX_ORDER];
+    double* V[ORC_MAX_ORDER];   /* last power-method vector per row (power_warm) */
     /* debug views of the last orc_snmc */
     int dbg_mode;
     double* dbg_H;
@@ -246,6 +256,7 @@ void orc_destroy(orc_state* s) {
         free(s->U[i]);
         free(s->row_ptr[i]);
         free(s->perm[i]);
+        free(s->V[i]);
     }
     free(s->idx);
     free(s->vals);
@@ -260,6 +271,8 @@ int orc_set_param(orc_state* s, const char* key, double value) {
     } else if (!strcmp(key, "power_iters")) {
         if (value < 1) return -1;
         s->power_iters = (int)value;
+    } else if (!strcmp(key, "power_warm")) {
+        s->power_warm = value != 0.0;
     } else if (!strcmp(key, "lp_exact")) {
         s->lp_exact = value != 0.0;
     } else if (!strcmp(key, "debug")) {
@@ -286,6 +299,8 @@ int orc_set_observed(orc_state* s, int64_t nnz, const int32_t* idx, const double
     for (int i = 0; i < N; ++i) {
         free(s->row_ptr[i]);
         free(s->perm[i]);
+        free(s->V[i]);       /* new observations: the power method starts cold again */
+        s->V[i] = NULL;
         s->row_ptr[i] = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s->dims[i] + 1));
         s->perm[i] = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz + 1));
         if (orc_bucket(N, nnz, s->idx, i, s->dims[i], s->row_ptr[i], s->perm[i]) != 0) return -1;
@@ -347,6 +362,16 @@ int64_t orc_row_update(int order, int mode, int rank, double lambda, int power_i
                        const double* y, const double* a, double* a_out, double* y_out,
                        double* H_out, double* grad_out, double* L_out, double* Lx_out,
                        double* beta_out) {
+    return orc_row_update_v(order, mode, rank, lambda, power_iters, lp_exact, U, n, idx, vals, q0, c, seed,
+                            ao_iter, inner, y, a, a_out, y_out, H_out, grad_out, L_out, Lx_out, beta_out, NULL);
+}
+
+int64_t orc_row_update_v(int order, int mode, int rank, double lambda, int power_iters, int lp_exact,
+                         const double* const* U, int64_t n, const int32_t* idx, const double* vals,
+                         int64_t q0, double c, uint64_t seed, uint64_t ao_iter, int inner,
+                         const double* y, const double* a, double* a_out, double* y_out,
+                         double* H_out, double* grad_out, double* L_out, double* Lx_out,
+                         double* beta_out, double* v_io) {
     const int N = order, R = rank;
     const double lam = lambda;
     for (int r = 0; r < R; ++r) {
@@ -390,7 +415,7 @@ int64_t orc_row_update(int order, int mode, int rank, double lambda, int power_i
     /* line 8: gradient = W + Z + lambda Y_l(p,:) */
     for (int r = 0; r < R; ++r) G[r] = W[r] + Z[r] + lam * y[r];
     /* line 10: L_p = max(eig(H_{l,p})) */
-    const double Lpm = orc_power_lmax(R, H, power_iters);
+    const double Lpm = orc_power_lmax_v(R, H, power_iters, v_io);
     const double L = lp_exact ? orc_jacobi_lmax(R, H) : Lpm;
     if (H_out) memcpy(H_out, H, sizeof(double) * (size_t)R * R);
     if (grad_out) memcpy(grad_out, G, sizeof(double) * (size_t)R);
@@ -426,6 +451,10 @@ int orc_snmc(orc_state* s, int mode, double c, uint64_t seed) {
     const int N = s->order, R = s->rank;
     const int64_t P = s->dims[mode];
     double* A = s->U[mode];                      /* A_l, updated in place */
+    if (s->power_warm && !s->V[mode]) {          /* first warm use: v0 = ones/sqrt(R) */
+        s->V[mode] = (double*)malloc(sizeof(double) * (size_t)P * (size_t)R);
+        for (int64_t q = 0; q < P * R; ++q) s->V[mode][q] = 1.0 / sqrt((double)R);
+    }
     double* Y = (double*)malloc(sizeof(double) * (size_t)P * (size_t)R);
     memcpy(Y, A, sizeof(double) * (size_t)P * (size_t)R); /* Y_0 = A_0 = A_* */
     const double* const* U = (const double* const*)s->U;
@@ -461,12 +490,13 @@ int orc_snmc(orc_state* s, int mode, double c, uint64_t seed) {
             double* anew = (double*)malloc(sizeof(double) * (size_t)R);
             double* ynew = (double*)malloc(sizeof(double) * (size_t)R);
             const int dbg = s->debug && l == s->max_inner - 1;
-            const int64_t k = orc_row_update(N, mode, R, s->lambda, s->power_iters, s->lp_exact, U, n,
-                                             ridx, rval, q0, c, seed, s->ao_iter, l, y, a, anew, ynew,
-                                             dbg ? s->dbg_H + p * R * R : NULL,
-                                             dbg ? s->dbg_grad + p * R : NULL,
-                                             dbg ? s->dbg_L + p : NULL, dbg ? s->dbg_Lx + p : NULL,
-                                             dbg ? s->dbg_beta + p : NULL);
+            const int64_t k = orc_row_update_v(N, mode, R, s->lambda, s->power_iters, s->lp_exact, U, n,
+                                               ridx, rval, q0, c, seed, s->ao_iter, l, y, a, anew, ynew,
+                                               dbg ? s->dbg_H + p * R * R : NULL,
+                                               dbg ? s->dbg_grad + p * R : NULL,
+                                               dbg ? s->dbg_L + p : NULL, dbg ? s->dbg_Lx + p : NULL,
+                                               dbg ? s->dbg_beta + p : NULL,
+                                               s->power_warm ? s->V[mode] + p * R : NULL);
             if (dbg) s->dbg_kp[p] = k > 0 ? k : orc_sample_count(c, n);
             if (k <= 0 && l == 0) skipped += 1;
             if (k != 0) visits += k > 0 ? k : orc_sample_count(c, n);

@@ -64,6 +64,11 @@ int orc_bucket(int order, int64_t nnz, const int32_t* idx, int mode, int64_t dim
 /* Power method for the largest eigenvalue of the symmetric R x R matrix H
  * (row-major), fixed iteration count (reading above). */
 double orc_power_lmax(int R, const double* H, int iters);
+/* The same from start vector v_io (NULL: ones/sqrt(R)); v_io receives the
+ * last normalised iterate.  A warm start of the next call on a nearby H (the
+ * estimation of L_p is an open topic of Sec. II-B; this reading keeps each
+ * row's last vector between S_NMC calls). */
+double orc_power_lmax_v(int R, const double* H, int iters, double* v_io);
 
 /* Largest eigenvalue of a symmetric matrix by cyclic Jacobi rotations. */
 double orc_jacobi_lmax(int R, const double* H);
@@ -79,6 +84,14 @@ int64_t orc_row_update(int order, int mode, int rank, double lambda, int power_i
                        const double* y, const double* a, double* a_out, double* y_out,
                        double* H_out, double* grad_out, double* L_out, double* Lx_out,
                        double* beta_out);
+/* The same with the power method started from v_io (NULL: cold start), which
+ * receives the row's last power-method vector. */
+int64_t orc_row_update_v(int order, int mode, int rank, double lambda, int power_iters, int lp_exact,
+                         const double* const* U, int64_t n, const int32_t* idx, const double* vals,
+                         int64_t q0, double c, uint64_t seed, uint64_t ao_iter, int inner,
+                         const double* y, const double* a, double* a_out, double* y_out,
+                         double* H_out, double* grad_out, double* L_out, double* Lx_out,
+                         double* beta_out, double* v_io);
 
 /* ---- whole-problem state (Algorithms 1-2) ---- */
 typedef struct orc_state orc_state;
@@ -86,6 +99,8 @@ typedef struct orc_state orc_state;
 orc_state* orc_create(int order, const int64_t* dims, int rank, double lambda);
 void orc_destroy(orc_state* s);
 /* keys: "max_inner", "power_iters", "lp_exact" (0 power method, 1 Jacobi),
+ *       "power_warm" (1: each row's power method starts from the vector its
+ *       previous update of this mode ended with; ones/sqrt(R) the first time),
  *       "debug" (1: keep per-row H, gradient, L of the last row update). */
 int orc_set_param(orc_state* s, const char* key, double value);
 /* Copies the COO tensor (idx[nnz][order], zero based) and buckets every mode. */

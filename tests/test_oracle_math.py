@@ -349,3 +349,55 @@ def test_planted_recovery_small(oracle_mod):
     assert small[19] < 0.5 * full[19]
     assert small[-1] < 0.1 * r0
     assert small[-1] < 1.5 * p.sigma
+
+
+# ---- warm-started power method (the cheaper-L_p topic of Sec. II-B) ----------
+
+def test_warm_power_method_continues_the_cold_iteration_exactly(oracle_mod):
+    oracle = oracle_mod
+    rng = np.random.default_rng(11)
+    for R in (1, 3, 8, 17):
+        A = rng.random((R, R + 3))
+        H = A @ A.T + 1e-3 * np.eye(R)
+        for t1, t2 in ((1, 9), (4, 6), (9, 1)):
+            mu1, v1 = oracle.power_lmax_v(H, t1)
+            mu2, v2 = oracle.power_lmax_v(H, t2, v1)
+            assert mu2 == oracle.power_lmax(H, t1 + t2)
+            assert abs(np.linalg.norm(v2) - 1.0) < 1e-12
+
+
+def test_warm_start_tracks_a_slowly_changing_matrix_better_than_cold(oracle_mod):
+    oracle = oracle_mod
+    rng = np.random.default_rng(12)
+    R = 16
+    A = rng.random((R, 40))
+    v = None
+    warm_err, cold_err = [], []
+    for _ in range(30):
+        A = A + 0.02 * rng.random(A.shape)         # the next minibatch's H is close to the last
+        H = A @ A.T + 1e-3 * np.eye(R)
+        exact = np.linalg.eigvalsh(H)[-1]
+        mu_w, v = oracle.power_lmax_v(H, 2, v)
+        warm_err.append((exact - mu_w) / exact)
+        cold_err.append((exact - oracle.power_lmax(H, 2)) / exact)
+    assert np.all(np.array(warm_err) >= -1e-12)    # Rayleigh quotients never exceed lambda_max
+    assert np.mean(warm_err[5:]) < 0.1 * np.mean(cold_err[5:])
+
+
+def test_oracle_warm_start_begins_cold_and_then_differs(oracle_mod):
+    oracle = oracle_mod
+    p = synth.planted_rank10_100cube()
+    runs = []
+    for warm in (0, 1):
+        o = oracle.Oracle(p.dims, p.rank, p.lam)
+        o.set_param("power_warm", warm)
+        o.set_param("power_iters", 3)
+        o.set_observed(p.idx_train, p.val_train.astype(np.float64))
+        o.init_factors(3)
+        o.snmc(0, p.c, seed=5)
+        first = o.get_factor(0).copy()
+        o.ao_iter = 1
+        o.snmc(0, p.c, seed=5)
+        runs.append((first, o.get_factor(0).copy()))
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])   # first call: v0 = ones/sqrt(R) both ways
+    assert not np.array_equal(runs[0][1], runs[1][1])       # second call starts from the kept vector
