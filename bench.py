@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default="zipf", choices=["zipf", "uber"],
                     help="zipf: Zipf(1.1) 10^4-cube, R=32; uber: the Uber-shaped 4-way timing twin")
     ap.add_argument("--rank", type=int, default=0, help="fitted rank (default: the workload's)")
+    ap.add_argument("--power-warm", type=int, default=0,
+                    help="N > 0: warm-started power method with N iterations (labelled variant)")
     # serving stream (continuous-batching completion server)
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead of the epoch bench")
     ap.add_argument("--serve-full", action="store_true",
@@ -84,6 +86,8 @@ def config(p, args):
         text = (f"zipf1.1 10000^3 tensor, R={p.rank}, {args.nnz // 1_000_000}M draws ({p.nnz} train), c=0.1, "
                 f"MAX_INNER=1, {storage} factor storage")
         l2 = "inputs larger than L2: 3 per-mode buckets of 16 B/entry (~4.7 GB) re-read every epoch"
+    if getattr(args, "power_warm", 0):
+        text += f", variant: warm-started power method, {args.power_warm} iterations"
     return {"workload": text, "dims": p.dims, "rank": p.rank, "nnz_train": p.nnz, "c": p.c, "lambda": p.lam,
             "step": f"one epoch = {T} AO iterations x {N} modes", "l2": l2,
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
@@ -278,6 +282,8 @@ def run_ntc(args):
     params = dict(profile=1)
     if args.storage_bf16:
         params["storage_bf16"] = 1
+    if args.power_warm:
+        params.update(power_warm=1, power_iters=args.power_warm)
     g = ntc.NTC(p.dims, p.rank, p.lam, stream=stream.cuda_stream, **params)
     g.set_observed(p.idx_train, p.val_train)
     fp32_peak = ntc.measure_fp32_peak(stream.cuda_stream)

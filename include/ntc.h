@@ -65,6 +65,11 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
  *                    copy (round-to-nearest-even of the float32 master)
  *   "init_seed"      seed of the initial factors drawn at ntc_set_observed (default 3)
  *   "keep_perm"      1: keep the bucket permutation for ntc_get_bucket (default 0)
+ *   "power_warm"     1: each row's power method for L_p starts from the vector
+ *                    that row's previous update of the same mode ended with
+ *                    (ones/sqrt(R) the first time and after ntc_set_observed);
+ *                    with "power_iters" lowered this is a cheaper L_p (Sec. II-B
+ *                    leaves cheaper L_p estimation open).  Default 0
  *   "cache_staging"  1: keep ntc_set_observed's staging copy of the observations
  *                    and its sort buffers (about nnz*(4N+20) bytes) for the next
  *                    call instead of allocating and freeing them each time

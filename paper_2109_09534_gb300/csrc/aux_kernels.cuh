@@ -281,6 +281,12 @@ __global__ void __launch_bounds__(kThreads) k_sum_partials(const double* partial
 // col}, key init_seed) with `row` the original row index, u = (word0 + 1/2)
 // 2^-32, drawn in double, stored rounded to float at the row's storage slot;
 // padding columns are zero.
+// Cold start of the warm-started power method: ones/sqrt(R) in the R columns.
+__global__ void k_fill_warm(float* V, int64_t rows, int R, int rp) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rows * rp; q += (int64_t)gridDim.x * blockDim.x)
+        V[q] = (int)(q % rp) < R ? 1.0f / sqrtf((float)R) : 0.f;
+}
+
 __global__ void k_init_factor(float* U, uint16_t* Ub, int64_t rows, int R, int rp, int mode,
                               const double* sum_vals, int64_t nnz, int order, uint32_t k0, uint32_t k1,
                               const int32_t* perm_rows) {

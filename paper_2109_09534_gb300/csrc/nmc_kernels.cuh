@@ -624,7 +624,7 @@ __device__ __forceinline__ void finish_row_warp(const ModeArgs& a, int p, const 
         const bool in = r < R;
         al[t] = in ? a.U[base + r] : 0.f;
         y[t] = in ? (a.read_y ? a.Y[base + r] : al[t]) : 0.f;
-        v[t] = in ? 1.0f / sqrtf((float)R) : 0.f;
+        v[t] = in ? (a.vwarm ? a.vwarm[base + r] : 1.0f / sqrtf((float)R)) : 0.f;
     }
     // for RP <= 32 lane r keeps row r of H in registers; x is read as float4
     // broadcasts (the sums run over c in the same order either way)
@@ -703,6 +703,13 @@ __device__ __forceinline__ void finish_row_warp(const ModeArgs& a, int p, const 
         const float inv = 1.0f / sqrtf(ww);
 #pragma unroll
         for (int t = 0; t < PER; ++t) v[t] = w[t] * inv;
+    }
+    if (a.vwarm) {   // the next update of this row starts from here
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int r = lane + 32 * t;
+            if (r < R) a.vwarm[base + r] = v[t];
+        }
     }
     const float L = mu;
     if (!(L > 0.f)) return;   // L_p <= 0: the row is skipped

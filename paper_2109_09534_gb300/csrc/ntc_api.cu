@@ -274,8 +274,16 @@ ntc_status run_snmc(ntc_handle* h, int mode, double c, uint64_t seed, uint64_t a
     if (st != NTC_OK) return st;
     const ModePlan& p = h->plan[mode];
     Launcher L = make_launcher(h);
+    if (h->power_warm && !h->warm_ready[mode]) {   // first warm use: v0 = ones/sqrt(R)
+        NTC_CUDA(h, h->vwarm[mode].ensure(sizeof(float) * (size_t)(h->dims[mode] * h->rp)));
+        k_fill_warm<<<grid_for(h->dims[mode] * h->rp), 256, 0, h->stream>>>(h->vwarm[mode].as<float>(), h->dims[mode],
+                                                                             h->rank, h->rp);
+        NTC_CUDA(h, cudaGetLastError());
+        h->warm_ready[mode] = true;
+    }
     for (int l = 0; l < h->max_inner; ++l) {
         ModeArgs a = mode_args(h, mode, l, seed, ao_iter);
+        a.vwarm = h->power_warm ? h->vwarm[mode].as<float>() : nullptr;
         NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, p, L, false));
         h->stats.visits += p.visits;
         h->stats.visits_heavy += p.visits_heavy;
@@ -405,6 +413,7 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
     std::swap(h->coo_val.bytes, cval.bytes);
     h->nnz = nnz;
     h->ao_iter = 0;
+    for (int i = 0; i < N; ++i) h->warm_ready[i] = false;   // new observations: cold power method again
     for (int i = 0; i < N; ++i) h->plan[i].valid = false;
     // factors set by the caller keep their values across the renumbering
     std::vector<std::vector<float>> kept(N);
@@ -601,6 +610,7 @@ int64_t handle_device_bytes(const ntc_handle* h) {
                    h->red.bytes + h->mask.bytes + h->stage_idx.bytes + h->stage_val.bytes + h->sort_k0.bytes +
                    h->sort_k1.bytes + h->sort_v0.bytes + h->sort_v1.bytes + h->sort_hist.bytes + h->sort_sums.bytes +
                    h->bad_flag.bytes + h->row_cnt.bytes + h->entry_tmp.bytes);
+    for (int i = 0; i < kMaxOrder; ++i) b += (int64_t)h->vwarm[i].bytes;
     return b;
 }
 
@@ -714,6 +724,8 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
         h->profile = v != 0.0;
     } else if (k == "keep_perm") {
         h->keep_perm = v != 0.0;
+    } else if (k == "power_warm") {
+        h->power_warm = v != 0.0 ? 1 : 0;
     } else if (k == "cache_staging") {
         h->cache_staging = v != 0.0 ? 1 : 0;
     } else if (k == "bracket_z") {

@@ -98,6 +98,10 @@ struct ntc_handle {
     // ntc_set_observed staging (the next COO) and radix-sort buffers, kept
     // between calls unless "cache_staging" is 0
     int cache_staging = 1;
+    // warm-started power method: last vector per row, per mode (storage order)
+    int power_warm = 0;
+    bool warm_ready[ntc::kMaxOrder] = {};
+    ntc::DevMem vwarm[ntc::kMaxOrder];
     ntc::DevMem stage_idx, stage_val, sort_k0, sort_k1, sort_v0, sort_v1, sort_hist, sort_sums, bad_flag, row_cnt,
         entry_tmp;
     // per-kernel event timing ("profile")

@@ -200,6 +200,7 @@ struct ModeArgs {
     int n_groups;
     float* partial2;          // [n_groups][pw]
     float* row_sum;           // [n_light + n_heavy][pw] reduced Gram/data sums: light rows, then split rows
+    float* vwarm;             // [rows][rp] (storage order): each row's last power-method vector, or null
     int n_light;
     unsigned long long* stat_fallback;  // counter of rows that used the exact selector
     uint8_t* mask_out;        // sampler-only mode: mask over bucket positions

@@ -121,6 +121,31 @@ def test_epoch_zipf_split_rows_and_mode_order(torch):
     assert st["visits"] == o.visits and st["rows_skipped"] == o.rows_skipped
 
 
+@pytest.mark.parametrize("rank", [10, 33])
+def test_warm_power_method_epochs(torch, rank):
+    """Warm-started power method (3 iterations from each row's last vector),
+    light and split rows, two epochs, against the oracle's same reading."""
+    p = synth.make_problem([60, 50, 40], rank, 30_000, sigma=0.01, test_frac=0.05, seed=40 + rank)
+    params = dict(power_warm=1, power_iters=3)
+    g, o = pair(p, torch, gparams=dict(params, heavy_rows=256, chunk=300), oparams=params)
+    for e in range(2):
+        g.epoch(0.25, seed=50 + e)
+        o.epoch(0.25, seed=50 + e)
+    for m in range(3):
+        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, (rank, m)
+    # new observations reset the kept vectors on both sides: the first epoch
+    # after them matches a cold run with the same iteration count
+    g2, o2 = pair(p, torch, gparams=dict(power_iters=3, heavy_rows=256, chunk=300), oparams=dict(power_iters=3))
+    g.set_observed(p.idx_train, p.val_train)
+    U0 = [g2.get_factor(m) for m in range(3)]
+    for m in range(3):
+        g.set_factor(m, U0[m])
+    g.set_param("power_warm", 1)
+    g.snmc(0, 0.25, seed=9)
+    g2.snmc(0, 0.25, seed=9)
+    np.testing.assert_array_equal(g.get_factor(0), g2.get_factor(0))
+
+
 @pytest.mark.parametrize("rank", [1, 3, 8, 10, 16, 17, 31, 33, 64])
 def test_ranks(torch, rank):
     p = synth.make_problem([60, 50, 40], rank, 30_000, sigma=0.01, test_frac=0.05, seed=rank)
