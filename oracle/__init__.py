@@ -61,6 +61,9 @@ def _lib(omp: bool = False):
                                  ctypes.c_int64, P, P]
         L.orc_power_lmax.restype = ctypes.c_double
         L.orc_power_lmax.argtypes = [ctypes.c_int, P, ctypes.c_int]
+        L.orc_perm_index.restype = ctypes.c_int64
+        L.orc_perm_index.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                     ctypes.c_int64, ctypes.c_int64]
         L.orc_power_lmax_v.restype = ctypes.c_double
         L.orc_power_lmax_v.argtypes = [ctypes.c_int, P, ctypes.c_int, P]
         L.orc_jacobi_lmax.restype = ctypes.c_double
@@ -146,6 +149,12 @@ def power_lmax(H: np.ndarray, iters: int = 10) -> float:
     """Power-method estimate of max eig(H) (Alg. 1 line 10, Sec. II-B item 4)."""
     H = np.ascontiguousarray(H, dtype=np.float64)
     return float(_lib().orc_power_lmax(H.shape[0], _ptr(H), iters))
+
+
+def perm_index(seed: int, mode: int, epoch: int, row: int, n: int, i: int) -> int:
+    """Epoch-permutation sampling: image of i under row `row`'s permutation of
+    [0, n) in epoch `epoch`."""
+    return int(_lib().orc_perm_index(seed, mode, epoch, row, n, i))
 
 
 def power_lmax_v(H: np.ndarray, iters: int, v: np.ndarray = None):

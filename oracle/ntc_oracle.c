@@ -75,6 +75,50 @@ static int orc_cmp_keypos(const void* a, const void* b) {
  * every k-subset is equally likely because the keys are i.i.d. uniform and
  * ties are broken by a fixed rule (Sec. II-B, "sample uniformly at random
  * B_{l,p} nonzero elements"). */
+/* Epoch-permutation variant of the sampling: within an epoch of T AO
+ * iterations every row is read in the order of one pseudo-random permutation
+ * and the minibatch slots take disjoint consecutive stretches of it (the
+ * epoch of Sec. IV touches every entry once).  The permutation of [0, n) is a
+ * 8-round balanced Feistel network on the smallest even number of bits (at
+ * least 8) that covers n, walked until the value falls below n; its eight round keys are
+ * the words of two Philox4x32-10 blocks (counters {0xF2000000 | mode, epoch,
+ * row, 0 or 1}, key seed) and its round function is the 32-bit finaliser of
+ * MurmurHash3 (Appleby), applied to the right half xor the round key. */
+static uint32_t orc_fmix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
+
+int64_t orc_perm_index(uint64_t seed, uint32_t mode, uint32_t epoch, uint32_t row, int64_t n, int64_t i) {
+    if (n <= 1) return 0;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t K[8];
+    for (uint32_t blk = 0; blk < 2; ++blk) {
+        const uint32_t ctr[4] = {0xF2000000u | mode, epoch, row, blk};
+        orc_philox4x32_10(ctr, key, K + 4 * blk);
+    }
+    int bits = 0;
+    while ((1ll << bits) < n) ++bits;         /* 2^bits >= n */
+    int half = (bits + 1) / 2;                 /* domain 2^(2 half) >= n ... */
+    if (half < 4) half = 4;                    /* ... and >= 256: short rows walk further */
+    const uint32_t mask = (1u << half) - 1u;
+    uint64_t x = (uint64_t)i;
+    do {
+        uint32_t L = (uint32_t)(x >> half), Rh = (uint32_t)x & mask;
+        for (int r = 0; r < 8; ++r) {
+            const uint32_t t = L ^ (orc_fmix32(Rh ^ K[r]) & mask);
+            L = Rh;
+            Rh = t;
+        }
+        x = ((uint64_t)L << half) | Rh;
+    } while (x >= (uint64_t)n);
+    return (int64_t)x;
+}
+
 int orc_sample_row(uint64_t seed, uint32_t mode, uint64_t ao_iter, uint32_t inner,
                    int64_t q0, int64_t n, int64_t k, int64_t* out) {
     if (n < 0 || k < 0 || k > n) return -1;
@@ -202,6 +246,7 @@ struct orc_state {
     int max_inner;
     int power_iters;
     int power_warm;     /* 1: each row's power method starts from its last vector */
+    int sampler;        /* 0: independent samples; 1: epoch permutation */
     int lp_exact;
     int debug;
     uint64_t ao_iter;
@@ -271,6 +316,9 @@ int orc_set_param(orc_state* s, const char* key, double value) {
     } else if (!strcmp(key, "power_iters")) {
         if (value < 1) return -1;
         s->power_iters = (int)value;
+    } else if (!strcmp(key, "sampler")) {
+        if (value != 0.0 && value != 1.0) return -1;
+        s->sampler = (int)value;
     } else if (!strcmp(key, "power_warm")) {
         s->power_warm = value != 0.0;
     } else if (!strcmp(key, "lp_exact")) {
@@ -372,6 +420,17 @@ int64_t orc_row_update_v(int order, int mode, int rank, double lambda, int power
                          const double* y, const double* a, double* a_out, double* y_out,
                          double* H_out, double* grad_out, double* L_out, double* Lx_out,
                          double* beta_out, double* v_io) {
+    return orc_row_update_s(order, mode, rank, lambda, power_iters, lp_exact, U, n, idx, vals, q0, c, seed,
+                            ao_iter, inner, y, a, a_out, y_out, H_out, grad_out, L_out, Lx_out, beta_out, v_io,
+                            0, 0, 1);
+}
+
+int64_t orc_row_update_s(int order, int mode, int rank, double lambda, int power_iters, int lp_exact,
+                         const double* const* U, int64_t n, const int32_t* idx, const double* vals,
+                         int64_t q0, double c, uint64_t seed, uint64_t ao_iter, int inner,
+                         const double* y, const double* a, double* a_out, double* y_out,
+                         double* H_out, double* grad_out, double* L_out, double* Lx_out,
+                         double* beta_out, double* v_io, int perm_sampler, int64_t row, int max_inner) {
     const int N = order, R = rank;
     const double lam = lambda;
     for (int r = 0; r < R; ++r) {
@@ -388,7 +447,17 @@ int64_t orc_row_update_v(int order, int mode, int rank, double lambda, int power
     double* kr = (double*)malloc(sizeof(double) * (size_t)R);
 
     /* line 5: M_hat_l(p,:) = sample(M(p,:)) */
-    orc_sample_row(seed, (uint32_t)mode, ao_iter, (uint32_t)inner, q0, n, k, sel);
+    if (perm_sampler) {
+        /* epoch e = floor(k / T) of T = ceil(1/c) AO iterations; slot s of
+         * the epoch takes positions pi((s k_p + j) mod n_p), j < k_p */
+        const uint64_t T = (uint64_t)ceil(1.0 / c - 1e-12);
+        const uint32_t epoch = (uint32_t)(ao_iter / T);
+        const int64_t s = (int64_t)(ao_iter % T) * max_inner + inner;
+        for (int64_t j = 0; j < k; ++j)
+            sel[j] = q0 + orc_perm_index(seed, (uint32_t)mode, epoch, (uint32_t)row, n, (s * k + j) % n);
+    } else {
+        orc_sample_row(seed, (uint32_t)mode, ao_iter, (uint32_t)inner, q0, n, k, sel);
+    }
 
     for (int64_t t = 0; t < k; ++t) {
         const int64_t j = sel[t] - q0;
@@ -490,13 +559,14 @@ int orc_snmc(orc_state* s, int mode, double c, uint64_t seed) {
             double* anew = (double*)malloc(sizeof(double) * (size_t)R);
             double* ynew = (double*)malloc(sizeof(double) * (size_t)R);
             const int dbg = s->debug && l == s->max_inner - 1;
-            const int64_t k = orc_row_update_v(N, mode, R, s->lambda, s->power_iters, s->lp_exact, U, n,
+            const int64_t k = orc_row_update_s(N, mode, R, s->lambda, s->power_iters, s->lp_exact, U, n,
                                                ridx, rval, q0, c, seed, s->ao_iter, l, y, a, anew, ynew,
                                                dbg ? s->dbg_H + p * R * R : NULL,
                                                dbg ? s->dbg_grad + p * R : NULL,
                                                dbg ? s->dbg_L + p : NULL, dbg ? s->dbg_Lx + p : NULL,
                                                dbg ? s->dbg_beta + p : NULL,
-                                               s->power_warm ? s->V[mode] + p * R : NULL);
+                                               s->power_warm ? s->V[mode] + p * R : NULL, s->sampler, p,
+                                               s->max_inner);
             if (dbg) s->dbg_kp[p] = k > 0 ? k : orc_sample_count(c, n);
             if (k <= 0 && l == 0) skipped += 1;
             if (k != 0) visits += k > 0 ? k : orc_sample_count(c, n);

@@ -51,6 +51,12 @@ int64_t orc_sample_count(double c, int64_t n);
 /* The k smallest (key, position) positions among bucket positions q0..q0+n-1,
  * written in ascending (key, position) order.  out[] holds absolute bucket
  * positions.  Returns 0, or -1 on bad arguments. */
+/* Epoch-permutation variant: image of i under the pseudo-random permutation
+ * of [0, n) of row `row` in epoch `epoch` (8-round Feistel network with cycle
+ * walking, round keys from two Philox blocks, MurmurHash3's finaliser as round
+ * function). */
+int64_t orc_perm_index(uint64_t seed, uint32_t mode, uint32_t epoch, uint32_t row, int64_t n, int64_t i);
+
 int orc_sample_row(uint64_t seed, uint32_t mode, uint64_t ao_iter, uint32_t inner,
                    int64_t q0, int64_t n, int64_t k, int64_t* out);
 
@@ -92,6 +98,15 @@ int64_t orc_row_update_v(int order, int mode, int rank, double lambda, int power
                          const double* y, const double* a, double* a_out, double* y_out,
                          double* H_out, double* grad_out, double* L_out, double* Lx_out,
                          double* beta_out, double* v_io);
+/* The same with the sampling reading chosen: perm_sampler 0 = independent
+ * samples, 1 = epoch permutation (slot (k mod T) * max_inner + inner of the
+ * epoch floor(k / T), T = ceil(1/c), of row `row`). */
+int64_t orc_row_update_s(int order, int mode, int rank, double lambda, int power_iters, int lp_exact,
+                         const double* const* U, int64_t n, const int32_t* idx, const double* vals,
+                         int64_t q0, double c, uint64_t seed, uint64_t ao_iter, int inner,
+                         const double* y, const double* a, double* a_out, double* y_out,
+                         double* H_out, double* grad_out, double* L_out, double* Lx_out,
+                         double* beta_out, double* v_io, int perm_sampler, int64_t row, int max_inner);
 
 /* ---- whole-problem state (Algorithms 1-2) ---- */
 typedef struct orc_state orc_state;
@@ -99,6 +114,9 @@ typedef struct orc_state orc_state;
 orc_state* orc_create(int order, const int64_t* dims, int rank, double lambda);
 void orc_destroy(orc_state* s);
 /* keys: "max_inner", "power_iters", "lp_exact" (0 power method, 1 Jacobi),
+ *       "sampler" (0: independent samples per AO iteration, 1: epoch
+ *       permutation -- the minibatches of an epoch are disjoint stretches of
+ *       one pseudo-random permutation of each row),
  *       "power_warm" (1: each row's power method starts from the vector its
  *       previous update of this mode ended with; ones/sqrt(R) the first time),
  *       "debug" (1: keep per-row H, gradient, L of the last row update). */

@@ -401,3 +401,40 @@ def test_oracle_warm_start_begins_cold_and_then_differs(oracle_mod):
         runs.append((first, o.get_factor(0).copy()))
     np.testing.assert_array_equal(runs[0][0], runs[1][0])   # first call: v0 = ones/sqrt(R) both ways
     assert not np.array_equal(runs[0][1], runs[1][1])       # second call starts from the kept vector
+
+
+# ---- epoch-permutation sampling variant (SURVEY-ranked next item; Sec. IV epoch) ----
+
+def test_epoch_permutation_update_matches_dense_masked_formula(oracle_mod):
+    """sampler = 1, c = 0.5, AO iteration 3 = slot 1 of epoch 1 (T = 2): M_hat
+    is rebuilt from the permutation's stretch, the step from dense formulas."""
+    rng = np.random.default_rng(19)
+    dims, R, lam = [6, 5, 4], 3, 0.05
+    cells = full_cells(dims)
+    idx = cells[rng.random(len(cells)) < 0.8]
+    vals = rng.random(idx.shape[0])
+    U = [rng.random((d, R)) for d in dims]
+    n, c, seed = 1, 0.5, 78
+    o = make_oracle(oracle_mod, dims, R, lam, idx, vals, U, lp_exact=1, sampler=1)
+    o.ao_iter = 3
+    o.snmc(n, c, seed)
+    row_ptr, perm = oracle_mod.bucket(idx, n, dims[n])
+    Mh = np.zeros(dims)
+    for p in range(dims[n]):
+        cnt = row_ptr[p + 1] - row_ptr[p]
+        k = oracle_mod.sample_count(c, cnt)
+        for j in range(k):
+            q = row_ptr[p] + oracle_mod.perm_index(seed, n, 1, p, cnt, (1 * k + j) % cnt)
+            Mh[tuple(idx[perm[q]])] = 1
+    X = np.zeros(dims)
+    X[tuple(idx.T)] = vals
+    K = kr_for_mode(U, n)
+    Mn, Xn = unfold(Mh, n), unfold(X, n)
+    grad = -(Mn * Xn - Mn * (U[n] @ K.T)) @ K + lam * U[n]
+    want = U[n].copy()
+    for p in range(dims[n]):
+        if Mn[p].sum() == 0:
+            continue
+        H = K.T @ np.diag(Mn[p]) @ K + lam * np.eye(R)
+        want[p] = np.maximum(0, U[n][p] - grad[p] / np.linalg.eigvalsh(H)[-1])
+    np.testing.assert_allclose(o.get_factor(n), want, rtol=1e-11, atol=1e-13)

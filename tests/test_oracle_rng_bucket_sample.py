@@ -111,3 +111,48 @@ def test_sample_streams_independent_across_mode_iter_inner(oracle_mod):
     for args in [(5, 1, 0, 0), (5, 0, 1, 0), (5, 0, 0, 1), (6, 0, 0, 0)]:
         other = oracle_mod.sample_row(*args, 0, 200, 20)
         assert set(other.tolist()) != set(base.tolist())
+
+
+# ---- epoch-permutation sampling variant ------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 9, 31, 32, 33, 100, 257, 1000, 4097])
+def test_epoch_permutation_is_a_bijection(oracle_mod, n):
+    oracle = oracle_mod
+    for (seed, mode, epoch, row) in [(1, 0, 0, 0), (2, 1, 5, 7), (2 ** 40 + 3, 2, 9, 123456)]:
+        img = [oracle.perm_index(seed, mode, epoch, row, n, i) for i in range(n)]
+        assert sorted(img) == list(range(n))
+
+
+@pytest.mark.parametrize("n,c", [(100, 0.1), (97, 0.2), (1000, 0.05), (64, 0.25), (10, 0.3)])
+def test_epoch_slots_are_disjoint_stretches(oracle_mod, n, c):
+    oracle = oracle_mod
+    k = oracle.sample_count(c, n)
+    T = int(np.ceil(1.0 / c - 1e-12))
+    seen = []
+    for s in range(T):
+        seen += [oracle.perm_index(9, 0, 4, 11, n, (s * k + j) % n) for j in range(k)]
+    if T * k <= n:
+        assert len(set(seen)) == T * k                       # one epoch reads an entry at most once
+    else:
+        assert len(set(seen)) == n                           # ... and every entry when slots wrap around
+
+
+def test_epoch_permutation_is_uniform_and_varies_with_its_counter(oracle_mod):
+    oracle = oracle_mod
+    n, trials = 10, 20000
+    first = np.bincount([oracle.perm_index(3, 0, e, 0, n, 0) for e in range(trials)], minlength=n)
+    chi2 = ((first - trials / n) ** 2 / (trials / n)).sum()
+    assert chi2 < 27.9                                       # chi^2_9 at p = 0.001
+    # pairs (pi(0), pi(1)) cover the 90 ordered pairs evenly
+    pairs = np.zeros((n, n))
+    for e in range(trials):
+        pairs[oracle.perm_index(3, 0, e, 1, n, 0), oracle.perm_index(3, 0, e, 1, n, 1)] += 1
+    cells = pairs[~np.eye(n, dtype=bool)]
+    chi2 = ((cells - trials / 90) ** 2 / (trials / 90)).sum()
+    assert chi2 < 137.2                                      # chi^2_89 at p = 0.001
+    base = [oracle.perm_index(3, 0, 0, 0, 1000, i) for i in range(50)]
+    for kw in [dict(seed=4), dict(mode=1), dict(epoch=1), dict(row=1)]:
+        a = dict(seed=3, mode=0, epoch=0, row=0)
+        a.update(kw)
+        other = [oracle.perm_index(a["seed"], a["mode"], a["epoch"], a["row"], 1000, i) for i in range(50)]
+        assert other != base, kw
