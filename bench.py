@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default="zipf", choices=["zipf", "uber"],
                     help="zipf: Zipf(1.1) 10^4-cube, R=32; uber: the Uber-shaped 4-way timing twin")
     ap.add_argument("--rank", type=int, default=0, help="fitted rank (default: the workload's)")
+    ap.add_argument("--sampler", default="independent", choices=["independent", "perm"],
+                    help="perm: epoch-permutation minibatches (labelled variant)")
     ap.add_argument("--power-warm", type=int, default=0,
                     help="N > 0: warm-started power method with N iterations (labelled variant)")
     # serving stream (continuous-batching completion server)
@@ -88,6 +90,8 @@ def config(p, args):
         l2 = "inputs larger than L2: 3 per-mode buckets of 16 B/entry (~4.7 GB) re-read every epoch"
     if getattr(args, "power_warm", 0):
         text += f", variant: warm-started power method, {args.power_warm} iterations"
+    if getattr(args, "sampler", "independent") == "perm":
+        text += ", variant: epoch-permutation minibatches (disjoint stretches of one permutation per row and epoch)"
     return {"workload": text, "dims": p.dims, "rank": p.rank, "nnz_train": p.nnz, "c": p.c, "lambda": p.lam,
             "step": f"one epoch = {T} AO iterations x {N} modes", "l2": l2,
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
@@ -284,6 +288,8 @@ def run_ntc(args):
         params["storage_bf16"] = 1
     if args.power_warm:
         params.update(power_warm=1, power_iters=args.power_warm)
+    if args.sampler == "perm":
+        params["sampler"] = 1
     g = ntc.NTC(p.dims, p.rank, p.lam, stream=stream.cuda_stream, **params)
     g.set_observed(p.idx_train, p.val_train)
     fp32_peak = ntc.measure_fp32_peak(stream.cuda_stream)

@@ -65,6 +65,12 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
  *                    copy (round-to-nearest-even of the float32 master)
  *   "init_seed"      seed of the initial factors drawn at ntc_set_observed (default 3)
  *   "keep_perm"      1: keep the bucket permutation for ntc_get_bucket (default 0)
+ *   "sampler"        0: independent minibatch per AO iteration (the reading of
+ *                    Alg. 1 line 5, default); 1: epoch permutation -- in each
+ *                    epoch of T = ceil(1/c) AO iterations a row is read in one
+ *                    keyed pseudo-random permutation (8-round Feistel network,
+ *                    counters {0xF2000000|mode, epoch, row, 0/1}) and minibatch
+ *                    slot s takes positions pi((s k_p + j) mod n_p), j < k_p
  *   "power_warm"     1: each row's power method for L_p starts from the vector
  *                    that row's previous update of the same mode ended with
  *                    (ones/sqrt(R) the first time and after ntc_set_observed);

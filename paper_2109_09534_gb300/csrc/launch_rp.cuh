@@ -43,13 +43,20 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         if (e != cudaSuccess) return e;
         if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;
     }
+    if (p.n_heavy > 0 && a.perm) {
+        // epoch-permutation variant: visits straight from the permutation
+        e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_perm_visits<EW><<<p.n_chunks, kThreads, 0, s>>>(a); });
+        if (e != cudaSuccess) return e;
+    }
     if (p.n_heavy > 0) {
-        e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
-        if (e != cudaSuccess) return e;
-        e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_heavy_sample<EW><<<p.n_chunks, kThreads, 0, s>>>(a); });
-        if (e != cudaSuccess) return e;
-        e = L.run(NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<EW><<<p.n_heavy, kThreads, 0, s>>>(a); });
-        if (e != cudaSuccess) return e;
+        if (!a.perm) {
+            e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
+            if (e != cudaSuccess) return e;
+            e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_heavy_sample<EW><<<p.n_chunks, kThreads, 0, s>>>(a); });
+            if (e != cudaSuccess) return e;
+            e = L.run(NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<EW><<<p.n_heavy, kThreads, 0, s>>>(a); });
+            if (e != cudaSuccess) return e;
+        }
         if (mask_only) {
             k_heavy_mask<EW><<<p.n_chunks + p.n_heavy, kThreads, 0, s>>>(a);
             ++*L.launches;

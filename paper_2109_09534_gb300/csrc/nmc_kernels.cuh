@@ -803,6 +803,23 @@ __global__ void __launch_bounds__(kLightThreads, 4) k_light(ModeArgs a) {
     const int n = (int)(a.row_ptr[row + 1] - q0);
     const uint32_t uq0 = (uint32_t)q0;
 
+    if (a.perm) {
+        // epoch-permutation variant: the slot's stretch of the row's permutation
+        const PermGen pg(a.ss.k0, a.ss.k1, a.ss.mode, a.perm_epoch, (uint32_t)row, (uint32_t)n);
+        const uint32_t s0 = (uint32_t)((a.perm_slot * k) % n);   // stretch start; s0 + j < 2n
+        pg.map_range(s0, threadIdx.x, (uint32_t)k, LT, [&](uint32_t j, uint32_t x) { vis[j] = (uint16_t)x; });
+        __syncthreads();
+        if (a.mask_out) {
+            for (int i = threadIdx.x; i < k; i += LT) a.mask_out[q0 + vis[i]] = 1;
+            return;
+        }
+        G gr;
+        gr.init();
+        auto getpos = [&](int v) -> uint32_t { return uq0 + vis[v]; };
+        gr.run(a, getpos, k, uni);
+        gr.reduce(red, a.row_sum + (size_t)blockIdx.x * G::PW);
+        return;
+    }
     // Alg. 1 line 5: the k smallest (key, position) of the row's n positions
     unsigned long long T = ~0ull;
     if (k < n) {
@@ -943,6 +960,31 @@ __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan
         if (ncand > cap) atomicOr(&a.flags[h], 1u);
     }
     return nsel;
+}
+
+// Epoch-permutation variant for split rows: chunk c of a row writes its share
+// [k cl / nch, k (cl+1) / nch) of the row's k visits, the slot's stretch of
+// the row's permutation, at the row's start (list of chunk c at vis_off[c]).
+// (templated on the entry width only so that each translation unit keeps its own copy)
+template <int EW>
+__global__ void __launch_bounds__(kThreads) k_perm_visits(ModeArgs a) {
+    const int c = blockIdx.x;
+    const int h = a.chunks[c].x;
+    const int4 hv = a.heavy[h];   // {row, k, first chunk, end chunk}
+    const int row = hv.x;
+    const int64_t k = hv.y, nch = hv.w - hv.z, cl = c - hv.z;
+    const int64_t rp = a.row_ptr[row];
+    const int64_t n = a.row_ptr[row + 1] - rp;
+    const int64_t jb = k * cl / nch, je = k * (cl + 1) / nch;
+    const PermGen pg(a.ss.k0, a.ss.k1, a.ss.mode, a.perm_epoch, (uint32_t)row, (uint32_t)n);
+    const uint32_t s0 = (uint32_t)((a.perm_slot * k) % n);   // stretch start; s0 + j < 2n < 2^32
+    const uint32_t urp = (uint32_t)rp;
+    pg.map_range(s0, (uint32_t)jb + threadIdx.x, (uint32_t)je, kThreads,
+                 [&](uint32_t j, uint32_t x) { a.vis[rp + j] = urp + x; });
+    if (threadIdx.x == 0) {
+        a.vis_cnt[c] = (uint32_t)(je - jb);
+        if (cl == 0) a.extra_cnt[h] = 0;
+    }
 }
 
 template <int EW>
@@ -1098,7 +1140,7 @@ __global__ void __launch_bounds__(GramNT<RP>::value, GramNT<RP>::blocks) k_heavy
     const uint32_t* list;
     int cnt;
     if (item < a.n_chunks) {
-        list = a.vis + a.chunks[item].y;
+        list = a.vis + (a.vis_off ? a.vis_off[item] : a.chunks[item].y);
         cnt = (int)a.vis_cnt[item];
     } else {
         const int h = item - a.n_chunks;
@@ -1174,7 +1216,7 @@ __global__ void k_heavy_mask(ModeArgs a) {
     const uint32_t* list;
     int cnt;
     if (item < a.n_chunks) {
-        list = a.vis + a.chunks[item].y;
+        list = a.vis + (a.vis_off ? a.vis_off[item] : a.chunks[item].y);
         cnt = (int)a.vis_cnt[item];
     } else {
         const int h = item - a.n_chunks;

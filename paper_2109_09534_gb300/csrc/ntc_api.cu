@@ -69,6 +69,7 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     std::vector<std::pair<int64_t, int32_t>> light;   // (n, row)
     std::vector<int32_t> light_k;
     std::vector<int4> chunks, caps, heavy, hcand, groups;
+    std::vector<int32_t> voff;   // epoch-permutation variant: chunk list starts
     std::vector<int2> heavy_groups;
     std::vector<longlong2> brk;
     int64_t visits = 0, visits_heavy = 0, updated = 0, skipped = 0, cand_total = 0, extra_total = 0;
@@ -118,6 +119,7 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
             int cap = hi > lo ? (int)std::ceil(expect + 8.0 * std::sqrt(expect) + 8.0) : 0;
             cap = (cap + 3) & ~3;
             chunks.push_back(make_int4(hidx, (int)pb, (int)pe, (int)cand_total));
+            voff.push_back((int32_t)(rp[r] + (k * j) / nch));
             caps.push_back(make_int4(cap, 0, 0, 0));
             cand_total += cap;
         }
@@ -155,6 +157,7 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     NTC_CUDA(h, up(p.light_rows, lrows.data(), lrows.size() * 4));
     NTC_CUDA(h, up(p.light_k, light_k.data(), light_k.size() * 4));
     NTC_CUDA(h, up(p.chunks, chunks.data(), chunks.size() * sizeof(int4)));
+    NTC_CUDA(h, up(p.vis_off, voff.data(), voff.size() * sizeof(int32_t)));
     NTC_CUDA(h, up(p.chunk_caps, caps.data(), caps.size() * sizeof(int4)));
     NTC_CUDA(h, up(p.heavy, heavy.data(), heavy.size() * sizeof(int4)));
     NTC_CUDA(h, up(p.bracket, brk.data(), brk.size() * sizeof(longlong2)));
@@ -269,6 +272,17 @@ Launcher make_launcher(ntc_handle* h) {
 }
 
 // Algorithm 1 on one mode at AO iteration ao_iter.
+// Epoch-permutation variant: epoch floor(k / T) and slot (k mod T) * MAX_INNER
+// + inner of AO iteration k, T = ceil(1/c) AO iterations per epoch.
+void set_perm(const ntc_handle* h, ModeArgs& a, const ModePlan& p, double c, uint64_t ao_iter, int inner) {
+    if (!h->sampler) return;
+    const uint64_t T = (uint64_t)std::ceil(1.0 / c - 1e-12);
+    a.perm = 1;
+    a.perm_epoch = (uint32_t)(ao_iter / T);
+    a.perm_slot = (int64_t)(ao_iter % T) * h->max_inner + inner;
+    a.vis_off = p.vis_off.as<int32_t>();
+}
+
 ntc_status run_snmc(ntc_handle* h, int mode, double c, uint64_t seed, uint64_t ao_iter) {
     ntc_status st = build_plan(h, mode, c);
     if (st != NTC_OK) return st;
@@ -284,6 +298,7 @@ ntc_status run_snmc(ntc_handle* h, int mode, double c, uint64_t seed, uint64_t a
     for (int l = 0; l < h->max_inner; ++l) {
         ModeArgs a = mode_args(h, mode, l, seed, ao_iter);
         a.vwarm = h->power_warm ? h->vwarm[mode].as<float>() : nullptr;
+        set_perm(h, a, p, c, ao_iter, l);
         NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, p, L, false));
         h->stats.visits += p.visits;
         h->stats.visits_heavy += p.visits_heavy;
@@ -726,6 +741,9 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
         h->keep_perm = v != 0.0;
     } else if (k == "power_warm") {
         h->power_warm = v != 0.0 ? 1 : 0;
+    } else if (k == "sampler") {
+        if (v != 0.0 && v != 1.0) return fail(h, NTC_ERR_ARG, "sampler must be 0 (independent) or 1 (epoch permutation)");
+        h->sampler = (int)v;
     } else if (k == "cache_staging") {
         h->cache_staging = v != 0.0 ? 1 : 0;
     } else if (k == "bracket_z") {
@@ -962,6 +980,7 @@ ntc_status ntc_sample_mask(ntc_handle* h, int mode, double c, uint64_t seed, uin
     NTC_CUDA(h, cudaMemsetAsync(h->mask.p, 0, (size_t)std::max<int64_t>(h->nnz, 1), h->stream));
     ModeArgs a = mode_args(h, mode, inner, seed, ao_iter);
     a.mask_out = h->mask.as<uint8_t>();
+    set_perm(h, a, h->plan[mode], c, ao_iter, inner);
     Launcher L = make_launcher(h);
     NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, h->plan[mode], L, true));
     NTC_CUDA(h, cudaMemcpyAsync(mask, h->mask.p, (size_t)h->nnz, cudaMemcpyDeviceToHost, h->stream));

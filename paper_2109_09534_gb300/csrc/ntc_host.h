@@ -51,6 +51,7 @@ struct ModePlan {
     int64_t cand_total = 0, extra_total = 0;
     int n_groups = 0;
     DevMem light_rows, light_k, chunks, chunk_caps, heavy, bracket, heavy_cand, groups, heavy_groups;
+    DevMem vis_off;   // per chunk: start of its visit list in the epoch-permutation variant
 };
 
 inline int pad_rank(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
@@ -100,6 +101,7 @@ struct ntc_handle {
     int cache_staging = 1;
     // warm-started power method: last vector per row, per mode (storage order)
     int power_warm = 0;
+    int sampler = 0;   // 0: independent samples; 1: epoch permutation
     bool warm_ready[ntc::kMaxOrder] = {};
     ntc::DevMem vwarm[ntc::kMaxOrder];
     ntc::DevMem stage_idx, stage_val, sort_k0, sort_k1, sort_v0, sort_v1, sort_hist, sort_sums, bad_flag, row_cnt,

@@ -108,6 +108,88 @@ struct KeyGen {
     }
 };
 
+// Epoch-permutation sampling variant: row `row`'s pseudo-random permutation
+// of [0, n) in epoch `epoch` -- an 8-round balanced Feistel network on at
+// least 8 bits (the smallest even number covering n), walked until the value
+// falls below n.  Round keys: the words of two Philox4x32-10 blocks with
+// counters {0xF2000000 | mode, epoch, row, 0 or 1} under the sampling seed;
+// round function: MurmurHash3's 32-bit finaliser (Appleby) of the right half
+// xor the round key.  The walk from i < n meets a value below n within one
+// cycle of the network's permutation, so it ends.
+__device__ __forceinline__ uint32_t fmix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
+
+struct PermGen {
+    uint32_t K[8];
+    uint32_t n, mask;
+    int half;
+    __device__ PermGen(uint32_t k0, uint32_t k1, uint32_t mode, uint32_t epoch, uint32_t row, uint32_t n_) : n(n_) {
+        const uint4 a = philox4(0xF2000000u | mode, epoch, row, 0u, k0, k1);
+        const uint4 b = philox4(0xF2000000u | mode, epoch, row, 1u, k0, k1);
+        K[0] = a.x; K[1] = a.y; K[2] = a.z; K[3] = a.w;
+        K[4] = b.x; K[5] = b.y; K[6] = b.z; K[7] = b.w;
+        int bits = 0;
+        while (bits < 32 && (1ull << bits) < (unsigned long long)n) ++bits;
+        half = (bits + 1) / 2;
+        if (half < 4) half = 4;
+        mask = (1u << half) - 1u;
+    }
+    // one pass of the network (a permutation of [0, 2^(2 half)))
+    __device__ __forceinline__ uint32_t pass(uint32_t x) const {
+        uint32_t L = x >> half, R = x & mask;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint32_t t = L ^ (fmix32(R ^ K[r]) & mask);
+            L = R;
+            R = t;
+        }
+        return (L << half) | R;
+    }
+    __device__ __forceinline__ uint32_t map(uint32_t i) const {
+        if (n <= 1) return 0u;
+        uint32_t x = i;
+        do x = pass(x);
+        while (x >= n);
+        return x;
+    }
+    // pi(s0 + j mod n) for j = j0, j0 + stride, ... < j1, each written by
+    // emit(j, pi): a lane walks its own value one pass per step and moves to
+    // its next j as soon as the value falls below n, so lanes of a warp do not
+    // wait for each other's walks.  Every thread of the warp must call it.
+    template <class Emit>
+    __device__ __forceinline__ void map_range(uint32_t s0, uint32_t j0, uint32_t j1, uint32_t stride,
+                                              const Emit& emit) const {
+        uint32_t j = j0;
+        bool have = j < j1;
+        auto start = [&](uint32_t jj) {
+            const uint32_t t = s0 + jj;
+            return t >= n ? t - n : t;
+        };
+        uint32_t x = have ? start(j) : 0u;
+        if (n <= 1) {
+            for (; j < j1; j += stride) emit(j, 0u);
+            return;
+        }
+        while (__any_sync(0xffffffffu, have)) {
+            if (have) {
+                x = pass(x);
+                if (x < n) {
+                    emit(j, x);
+                    j += stride;
+                    have = j < j1;
+                    if (have) x = start(j);
+                }
+            }
+        }
+    }
+};
+
 // ---- bfloat16 storage helpers (round to nearest even on store).
 __device__ __forceinline__ float4 bf16x4_to_f32(uint2 v) {
     float4 r;
@@ -201,6 +283,12 @@ struct ModeArgs {
     float* partial2;          // [n_groups][pw]
     float* row_sum;           // [n_light + n_heavy][pw] reduced Gram/data sums: light rows, then split rows
     float* vwarm;             // [rows][rp] (storage order): each row's last power-method vector, or null
+    // epoch-permutation sampling variant: slot perm_slot of epoch perm_epoch;
+    // split rows' visits are stored from the row's start, chunk c's at vis_off[c]
+    int perm;
+    uint32_t perm_epoch;
+    int64_t perm_slot;
+    const int32_t* vis_off;
     int n_light;
     unsigned long long* stat_fallback;  // counter of rows that used the exact selector
     uint8_t* mask_out;        // sampler-only mode: mask over bucket positions

@@ -273,3 +273,47 @@ def test_edge_cases(torch):
         o.epoch(c, seed=3)
         for m in range(3):
             assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, (c, m)
+
+
+# ---- epoch-permutation sampling variant --------------------------------------------
+
+def perm_mask(idx, mode, dim, c, seed, ao_iter, inner, max_inner=1):
+    """The variant's sample of every row of `mode`, as a mask over bucket positions (oracle)."""
+    row_ptr, _ = oracle.bucket(idx, mode, dim)
+    T = int(np.ceil(1.0 / c - 1e-12))
+    epoch, slot = ao_iter // T, (ao_iter % T) * max_inner + inner
+    mask = np.zeros(idx.shape[0], dtype=np.uint8)
+    for r in range(dim):
+        q0, n = int(row_ptr[r]), int(row_ptr[r + 1] - row_ptr[r])
+        k = oracle.sample_count(c, n)
+        for j in range(k):
+            mask[q0 + oracle.perm_index(seed, mode, epoch, r, n, (slot * k + j) % n)] = 1
+    return mask
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_epoch_permutation_sampler_bit_exact(torch, split):
+    p = small_zipf(nnz=60_000, dim=400)
+    g = ntc.NTC(p.dims, p.rank, p.lam, stream=torch.cuda.current_stream().cuda_stream, sampler=1,
+                **(dict(heavy_rows=128, chunk=300) if split else {}))
+    g.set_observed(p.idx_train, p.val_train)
+    c, seed = 0.25, 4242
+    for m in range(3):
+        epoch_total = np.zeros(p.nnz, np.int32)
+        for it in range(4, 8):                       # AO iterations 4..7 = epoch 1 (T = 4)
+            got = g.sample_mask(m, c, seed, it, 0, p.nnz)
+            np.testing.assert_array_equal(got, perm_mask(p.idx_train, m, p.dims[m], c, seed, it, 0))
+            epoch_total += got
+        assert epoch_total.max() == 1                # the epoch's minibatches are disjoint
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_epoch_permutation_epoch_parity(torch, split):
+    p = small_zipf(nnz=120_000, dim=600)
+    gp = dict(sampler=1, **(dict(heavy_rows=128, chunk=700) if split else {}))
+    g, o = pair(p, torch, gparams=gp, oparams=dict(sampler=1))
+    for e in range(2):
+        g.epoch(0.2, seed=31 + e)
+        o.epoch(0.2, seed=31 + e)
+    for m in range(3):
+        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
