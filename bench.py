@@ -513,7 +513,8 @@ def run_study(args):
             vals = (p0.val_train + sigma * rng.standard_normal(p0.val_train.shape)).astype(np.float32)
             clean = p0.val_test_clean
             for c in cs:
-                g = ntc.NTC(dims, R, p0.lam, stream=stream, init_seed=3 + trial)
+                g = ntc.NTC(dims, R, p0.lam, stream=stream, init_seed=3 + trial,
+                            sampler=1 if args.sampler == "perm" else 0)
                 g.set_observed(p0.idx_train, vals)
                 curve = {}
                 for e in range(1, args.study_epochs + 1):
@@ -532,7 +533,7 @@ def run_study(args):
             "config": {"workload": f"planted rank-{R} U[0,1] tensor of MovieLens-10M shape {dims}, "
                                    f"{args.study_nnz} uniform draws (1% held out), lambda 1e-3, fitted R = {R}, "
                                    f"SNR {snrs_db} dB, c {cs}, {args.study_trials} trials, "
-                                   f"{args.study_epochs} epochs"},
+                                   f"{args.study_epochs} epochs, {args.sampler} minibatches"},
             "rre": table, "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
 
