@@ -88,19 +88,23 @@ __device__ unsigned long long block_select_kth(const Get& get, int n, int k, uns
 // block_select_kth when the boundary bin holds more than kSelCap items.
 //   digit(c) -> bin in [0, kSelBins), non-decreasing in c
 //   binmax(b) -> a composite >= every item of bins <= b and < every item of bins > b
-// Shared memory: hist kSelBins + 16 unsigned, mem kSelCap composites.
+// Shared memory: hist kSelPad + 16 unsigned, mem kSelCap composites.
 constexpr int kSelBins = 4096;
+constexpr int kSelPad = kSelBins + kSelBins / 32;   // one pad word per 32 bins
 constexpr int kSelCap = 512;
+// bin b lives at b + b / 32, so that the bins a thread owns, read one by one,
+// start in a different bank for every lane
+__device__ __forceinline__ int sel_slot(unsigned b) { return (int)(b + (b >> 5)); }
 
 template <int NTH = kThreads, class Get, class Digit, class BinMax>
 __device__ unsigned long long block_select_digit(const Get& get, int n, int m, const Digit& digit,
                                                  const BinMax& binmax, unsigned* hist,
                                                  unsigned long long* mem, int* scan_tmp) {
     constexpr int PER = kSelBins / NTH;
-    static_assert(PER * NTH == kSelBins && PER % 4 == 0, "bins per thread");
+    static_assert(PER * NTH == kSelBins && kSelPad % 4 == 0, "bins per thread");
     const int tid = threadIdx.x;
-    for (int i = tid; i < kSelBins / 4; i += NTH) reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
-    if (tid == 0) hist[kSelBins + 3] = 0u;
+    for (int i = tid; i < kSelPad / 4; i += NTH) reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) hist[kSelPad + 3] = 0u;
     __syncthreads();
     for (int base = 0; base < n; base += NTH * 8) {
         unsigned long long c[8];
@@ -111,19 +115,15 @@ __device__ unsigned long long block_select_digit(const Get& get, int n, int m, c
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            if (c[u] != ~0ull) atomicAdd(&hist[digit(c[u])], 1u);
+            if (c[u] != ~0ull) atomicAdd(&hist[sel_slot(digit(c[u]))], 1u);
     }
     __syncthreads();
     unsigned loc[PER];
     int own = 0;
 #pragma unroll
-    for (int i = 0; i < PER; i += 4) {
-        const uint4 v = reinterpret_cast<const uint4*>(hist + tid * PER)[i / 4];
-        loc[i] = v.x;
-        loc[i + 1] = v.y;
-        loc[i + 2] = v.z;
-        loc[i + 3] = v.w;
-        own += (int)(v.x + v.y + v.z + v.w);
+    for (int i = 0; i < PER; ++i) {
+        loc[i] = hist[sel_slot((unsigned)(tid * PER + i))];
+        own += (int)loc[i];
     }
     int total;
     const int excl = block_exclusive_scan<NTH>(own, scan_tmp, &total);
@@ -132,16 +132,16 @@ __device__ unsigned long long block_select_digit(const Get& get, int n, int m, c
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             if (cum < m && m <= cum + (int)loc[i]) {
-                hist[kSelBins] = (unsigned)(tid * PER + i);   // bin
-                hist[kSelBins + 1] = (unsigned)cum;           // items below the bin
-                hist[kSelBins + 2] = loc[i];                  // items in the bin
+                hist[kSelPad] = (unsigned)(tid * PER + i);   // bin
+                hist[kSelPad + 1] = (unsigned)cum;           // items below the bin
+                hist[kSelPad + 2] = loc[i];                  // items in the bin
             }
             cum += (int)loc[i];
         }
     }
     __syncthreads();
-    const unsigned b = hist[kSelBins];
-    const int below = (int)hist[kSelBins + 1], cnt = (int)hist[kSelBins + 2];
+    const unsigned b = hist[kSelPad];
+    const int below = (int)hist[kSelPad + 1], cnt = (int)hist[kSelPad + 2];
     const int need = m - below;   // 1 <= need <= cnt
     if (need == cnt) return binmax(b);
     if (cnt > kSelCap) {
@@ -157,10 +157,10 @@ __device__ unsigned long long block_select_digit(const Get& get, int n, int m, c
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            if (c[u] != ~0ull && digit(c[u]) == b) mem[atomicAdd(&hist[kSelBins + 3], 1u)] = c[u];
+            if (c[u] != ~0ull && digit(c[u]) == b) mem[atomicAdd(&hist[kSelPad + 3], 1u)] = c[u];
     }
     __syncthreads();
-    unsigned long long* res = reinterpret_cast<unsigned long long*>(hist + kSelBins + 4);   // 8-byte aligned
+    unsigned long long* res = reinterpret_cast<unsigned long long*>(hist + kSelPad + 4);   // 8-byte aligned
     for (int t = tid; t < cnt; t += NTH) {
         const unsigned long long ct = mem[t];
         int r = 0;
@@ -774,7 +774,7 @@ struct LightSmem {
     static constexpr size_t VIS = kLightMax * 2;
     // keys, then the select's histogram and boundary-bin members
     static constexpr size_t KEYS = kLightMax * 4;
-    static constexpr size_t SEL = KEYS + (size_t)(kSelBins + 16) * 4 + (size_t)kSelCap * 8;
+    static constexpr size_t SEL = KEYS + (size_t)(kSelPad + 16) * 4 + (size_t)kSelCap * 8;
     __host__ __device__ static constexpr size_t union_bytes(int no) {
         return G::region_bytes(no) > SEL ? G::region_bytes(no) : SEL;
     }
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(kLightThreads, 4) k_light(ModeArgs a) {
     unsigned char* uni = smem_raw + S::VIS;
     uint32_t* keys = reinterpret_cast<uint32_t*>(uni);
     unsigned* hist = reinterpret_cast<unsigned*>(uni + S::KEYS);
-    unsigned long long* mem = reinterpret_cast<unsigned long long*>(hist + kSelBins + 16);
+    unsigned long long* mem = reinterpret_cast<unsigned long long*>(hist + kSelPad + 16);
     float* red = reinterpret_cast<float*>(uni);
     int* scan_tmp = reinterpret_cast<int*>(uni + S::union_bytes(no));
 
@@ -999,7 +999,7 @@ __global__ void __launch_bounds__(kThreads) k_heavy_sample(ModeArgs a) {
 // recomputed keys and its chunk lists are rewritten.
 template <int EW>
 __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
-    __shared__ __align__(16) unsigned hist[kSelBins + 16];
+    __shared__ __align__(16) unsigned hist[kSelPad + 16];
     __shared__ unsigned long long mem[kSelCap];
     __shared__ int scan_tmp[kThreads / 32 + 1];
     __shared__ int red_i[2][kThreads / 32];
