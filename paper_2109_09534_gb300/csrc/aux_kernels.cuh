@@ -11,6 +11,12 @@ namespace ntc {
 constexpr int kSortIPT = 16;                       // keys per thread per tile
 constexpr int kSortTile = kThreads * kSortIPT;     // 4096 keys per tile
 
+// Storage row of each original row, per mode (factor rows are stored in
+// descending order of their observation counts).
+struct RowMaps {
+    const int32_t* inv[kMaxOrder];   // original row -> storage row, per mode
+};
+
 // Any index outside [0, dims[i]) sets *bad.
 __global__ void k_validate(const int32_t* idx, int64_t n, int order, const int64_t* dims_dev,
                            unsigned* bad) {
@@ -126,6 +132,111 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* kin,
     }
 }
 
+// Keys of `mode` alone (the first pass of the entry sort builds its payloads).
+__global__ void k_extract_mode(const int32_t* idx, int64_t n, int order, int mode, uint32_t* keys) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        keys[e] = (uint32_t)idx[e * order + mode];
+}
+
+// The same stable scatter with 16-byte bucket entries as payloads, so that
+// the last pass writes the bucket directly.  With FROM_COO (the first pass)
+// a key's entry is built from its COO row: the other modes' indices mapped to
+// storage rows (slot w holds mode w, or w + 1 past `mode`), then the value.
+// Dynamic shared memory: kEntScatterSmem bytes.
+constexpr size_t kEntScatterSmem = (size_t)(kThreads / 32) * 256 * 4 + (size_t)kSortTile * 4 +
+                                   (size_t)kSortTile * 16 + 256 * 4 + (kThreads / 32 + 1) * 4;
+template <bool FROM_COO>
+__global__ void __launch_bounds__(kThreads, 2) k_radix_scatter_ent(const uint32_t* kin, const uint4* pin,
+                                                                   uint32_t* kout, uint4* pout, int64_t n, int shift,
+                                                                   const uint32_t* offs, int ntiles, const int32_t* idx,
+                                                                   const float* vals, int order, int mode,
+                                                                   RowMaps maps) {
+    extern __shared__ __align__(16) unsigned char es[];
+    unsigned(*wh)[256] = reinterpret_cast<unsigned(*)[256]>(es);
+    uint32_t* sk = reinterpret_cast<uint32_t*>(es + (kThreads / 32) * 256 * 4);
+    uint4* sp = reinterpret_cast<uint4*>(sk + kSortTile);
+    int* gbase = reinterpret_cast<int*>(sp + kSortTile);
+    int* scan_tmp = gbase + 256;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + (int64_t)warp * (32 * kSortIPT);
+    uint32_t key[kSortIPT];
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        key[r] = i < n ? kin[i] : 0u;
+    }
+    for (int d = lane; d < 256; d += 32) wh[warp][d] = 0;
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        const bool valid = base + r * 32 + lane < n;
+        const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & lt) == 0) wh[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        int cnt = 0;
+        for (int w = 0; w < kThreads / 32; ++w) cnt += (int)wh[w][d];
+        int tot;
+        const int start = block_exclusive_scan(cnt, scan_tmp, &tot);
+        gbase[d] = (int)offs[(int64_t)d * ntiles + blockIdx.x] - start;
+        unsigned run = (unsigned)start;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const unsigned t = wh[w][d];
+            wh[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    // ranks first (keys staged), then each payload loaded once and staged at
+    // its key's slot, so that no thread holds all of its payloads at once
+    unsigned pos[kSortIPT];
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        const bool valid = base + r * 32 + lane < n;
+        const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        pos[r] = 0;
+        if (valid) pos[r] = wh[warp][d] + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wh[warp][d] += __popc(peers);
+        __syncwarp();
+        if (valid) sk[pos[r]] = key[r];
+    }
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        if (i < n) {
+            uint4 pay;
+            if constexpr (FROM_COO) {
+                uint32_t w[3];
+#pragma unroll
+                for (int sl = 0; sl < 3; ++sl) {
+                    const int src = sl + (sl >= mode ? 1 : 0);
+                    w[sl] = src < order ? (uint32_t)maps.inv[src][idx[i * order + src]] : 0u;
+                }
+                pay = make_uint4(w[0], w[1], w[2], __float_as_uint(vals[i]));
+            } else {
+                pay = pin[i];
+            }
+            sp[pos[r]] = pay;
+        }
+    }
+    __syncthreads();
+    const int tn = (int)min((int64_t)kSortTile, n - tile0);
+    for (int i = threadIdx.x; i < tn; i += kThreads) {
+        const uint32_t k = sk[i];
+        const int64_t g = (int64_t)gbase[(k >> shift) & 255u] + i;
+        kout[g] = k;
+        pout[g] = sp[i];
+    }
+}
+
 // Exclusive scan of n uint32 values (n < 2^31), three phases: block sums,
 // a one-block scan of the block sums, block-local scans with carry-in.
 constexpr int kScanBlock = 2048;
@@ -216,9 +327,6 @@ __global__ void __launch_bounds__(256) k_count_rows(const int32_t* idx, int64_t 
     }
 }
 
-struct RowMaps {
-    const int32_t* inv[kMaxOrder];   // original row -> storage row, per mode
-};
 
 // Bucket entries of `mode` (the other modes' indices mapped to their storage
 // rows, then the value) in input order, with coalesced reads of the COO;

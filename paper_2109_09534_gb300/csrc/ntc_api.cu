@@ -323,6 +323,56 @@ ntc_status reset_stats(ntc_handle* h) {
 }
 
 // Stable LSD radix sort of (key = row index of `mode`, payload = entry index).
+// Bucket of `mode` by a stable LSD radix sort of (row, entry) pairs: the
+// first pass builds the 16-byte entries from the COO, the last writes them in
+// bucket order (passes alternate between entry_tmp and the bucket so that the
+// last lands in the bucket).  *keys_out: the sorted rows.
+ntc_status sort_mode_entries(ntc_handle* h, int mode, const RowMaps& maps, DevMem& k0, DevMem& k1, DevMem& hist,
+                             DevMem& sums, uint32_t** keys_out) {
+    const int64_t n = h->nnz;
+    cudaStream_t s = h->stream;
+    static bool attr = false;
+    if (!attr) {
+        NTC_CUDA(h, set_smem(k_radix_scatter_ent<true>, kEntScatterSmem));
+        NTC_CUDA(h, set_smem(k_radix_scatter_ent<false>, kEntScatterSmem));
+        attr = true;
+    }
+    NTC_CUDA(h, h->entry_tmp.ensure(sizeof(uint4) * (size_t)std::max<int64_t>(n, 1)));
+    k_extract_mode<<<grid_for(n), 256, 0, s>>>(h->coo_idx.as<int32_t>(), n, h->order, mode, k0.as<uint32_t>());
+    int bits = 1;
+    while (bits < 31 && (1ll << bits) < h->dims[mode]) ++bits;
+    const int passes = (bits + 7) / 8;
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    const int64_t nh = (int64_t)ntiles * 256;
+    const int nb = (int)((nh + kScanBlock - 1) / kScanBlock);
+    uint32_t *kin = k0.as<uint32_t>(), *kout = k1.as<uint32_t>();
+    uint4* bucket = h->bucket[mode].as<uint4>();
+    uint4* tmp = h->entry_tmp.as<uint4>();
+    uint4* pin = nullptr;
+    uint4* pout = passes % 2 == 1 ? bucket : tmp;
+    for (int pass = 0; pass < passes && n > 0; ++pass) {
+        const int shift = 8 * pass;
+        k_radix_hist<<<ntiles, kThreads, 0, s>>>(kin, n, shift, hist.as<uint32_t>(), ntiles);
+        k_scan_sums<<<nb, kThreads, 0, s>>>(hist.as<uint32_t>(), nh, sums.as<uint32_t>());
+        k_scan_top<<<1, kThreads, 0, s>>>(sums.as<uint32_t>(), nb);
+        k_scan_apply<<<nb, kThreads, 0, s>>>(hist.as<uint32_t>(), nh, sums.as<uint32_t>(), hist.as<uint32_t>() + nh);
+        if (pass == 0)
+            k_radix_scatter_ent<true><<<ntiles, kThreads, kEntScatterSmem, s>>>(
+                kin, nullptr, kout, pout, n, shift, hist.as<uint32_t>() + nh, ntiles, h->coo_idx.as<int32_t>(),
+                h->coo_val.as<float>(), h->order, mode, maps);
+        else
+            k_radix_scatter_ent<false><<<ntiles, kThreads, kEntScatterSmem, s>>>(
+                kin, pin, kout, pout, n, shift, hist.as<uint32_t>() + nh, ntiles, nullptr, nullptr, h->order, mode,
+                maps);
+        std::swap(kin, kout);
+        pin = pout;
+        pout = pout == bucket ? tmp : bucket;
+    }
+    NTC_CUDA(h, cudaGetLastError());
+    *keys_out = kin;
+    return NTC_OK;
+}
+
 ntc_status sort_mode(ntc_handle* h, int mode, DevMem& k0, DevMem& k1, DevMem& v0, DevMem& v1, DevMem& hist,
                      DevMem& sums, uint32_t** keys_out, uint32_t** perm_out) {
     const int64_t n = h->nnz;
@@ -469,20 +519,25 @@ ntc_status set_observed_impl(ntc_handle* h, int64_t nnz, const int32_t* idx, con
     const size_t nb4 = sizeof(uint32_t) * (size_t)std::max<int64_t>(nnz, 1);
     NTC_CUDA(h, k0.ensure(nb4));
     NTC_CUDA(h, k1.ensure(nb4));
-    NTC_CUDA(h, v0.ensure(nb4));
-    NTC_CUDA(h, v1.ensure(nb4));
+    if (!(ew_of(N) == 4 && !h->keep_perm)) {   // the permutation path (orders > 4 or a kept permutation)
+        NTC_CUDA(h, v0.ensure(nb4));
+        NTC_CUDA(h, v1.ensure(nb4));
+    }
     const int64_t ntiles = (nnz + kSortTile - 1) / kSortTile;
     NTC_CUDA(h, hist.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(2 * ntiles * 256, 1)));
     NTC_CUDA(h, sums.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles * 256 / kScanBlock + 2, 1)));
     const int EW = ew_of(N);
     for (int i = 0; i < N; ++i) {
         uint32_t *keys = nullptr, *perm = nullptr;
-        ntc_status st = sort_mode(h, i, k0, k1, v0, v1, hist, sums, &keys, &perm);
+        NTC_CUDA(h, h->bucket[i].ensure((size_t)EW * 4 * (size_t)std::max<int64_t>(nnz, 1)));
+        // orders 2-4 without a kept permutation: entries ride through the sort
+        const bool ride = EW == 4 && !h->keep_perm;
+        ntc_status st = ride ? sort_mode_entries(h, i, maps, k0, k1, hist, sums, &keys)
+                             : sort_mode(h, i, k0, k1, v0, v1, hist, sums, &keys, &perm);
         if (st != NTC_OK) return st;
         NTC_CUDA(h, h->row_ptr[i].ensure(sizeof(int64_t) * (size_t)(h->dims[i] + 1)));
         k_row_ptr<<<grid_for(nnz + 1), 256, 0, s>>>(keys, nnz, h->dims[i], h->row_ptr[i].as<int64_t>());
-        NTC_CUDA(h, h->bucket[i].ensure((size_t)EW * 4 * (size_t)std::max<int64_t>(nnz, 1)));
-        if (nnz > 0) {
+        if (nnz > 0 && !ride) {
             NTC_CUDA(h, h->entry_tmp.ensure((size_t)EW * 4 * (size_t)nnz));
             if (EW == 4) {
                 k_build_entries<4><<<grid_for(nnz), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), nnz,
