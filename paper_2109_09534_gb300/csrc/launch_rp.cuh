@@ -12,16 +12,17 @@ namespace ntc {
 template <int RP, int EW, bool BF, int NOR>
 cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, bool mask_only) {
     cudaStream_t s = L.s;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e;
+    // kernel attributes once per process (handles may run on several threads)
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
         constexpr int nomax = Gram<RP, EW, BF>::NOMAX;
-        if ((e = set_smem(k_light<RP, EW, BF, NOR>, LightSmem<RP, EW, BF, NOR>::bytes(nomax))) != cudaSuccess) return e;
-        if ((e = set_smem(k_heavy_gram<RP, EW, BF, NOR>, HeavyGramSmem<RP, EW, BF, NOR>::bytes(nomax))) != cudaSuccess)
-            return e;
-        if ((e = set_smem(k_rows_finish<RP>, RowFinish<RP>::bytes())) != cudaSuccess) return e;
-        attr = true;
-    }
+        cudaError_t e = set_smem(k_light<RP, EW, BF, NOR>, LightSmem<RP, EW, BF, NOR>::bytes(nomax));
+        if (e == cudaSuccess) e = set_smem(k_heavy_gram<RP, EW, BF, NOR>, HeavyGramSmem<RP, EW, BF, NOR>::bytes(nomax));
+        if (e == cudaSuccess) e = set_smem(k_rows_finish<RP>, RowFinish<RP>::bytes());
+        attr_err = e;
+    });
+    if (attr_err != cudaSuccess) return attr_err;
     cudaError_t e = cudaSuccess;
     const bool fork = p.n_light > 0 && p.n_heavy > 0 && L.h->overlap;
     if (fork) {

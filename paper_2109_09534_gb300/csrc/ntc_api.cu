@@ -331,12 +331,14 @@ ntc_status sort_mode_entries(ntc_handle* h, int mode, const RowMaps& maps, DevMe
                              DevMem& sums, uint32_t** keys_out) {
     const int64_t n = h->nnz;
     cudaStream_t s = h->stream;
-    static bool attr = false;
-    if (!attr) {
-        NTC_CUDA(h, set_smem(k_radix_scatter_ent<true>, kEntScatterSmem));
-        NTC_CUDA(h, set_smem(k_radix_scatter_ent<false>, kEntScatterSmem));
-        attr = true;
-    }
+    // once per process (admissions of a server may bucket on several threads)
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = set_smem(k_radix_scatter_ent<true>, kEntScatterSmem);
+        if (attr_err == cudaSuccess) attr_err = set_smem(k_radix_scatter_ent<false>, kEntScatterSmem);
+    });
+    NTC_CUDA(h, attr_err);
     NTC_CUDA(h, h->entry_tmp.ensure(sizeof(uint4) * (size_t)std::max<int64_t>(n, 1)));
     k_extract_mode<<<grid_for(n), 256, 0, s>>>(h->coo_idx.as<int32_t>(), n, h->order, mode, k0.as<uint32_t>());
     int bits = 1;

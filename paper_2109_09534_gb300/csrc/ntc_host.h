@@ -5,6 +5,7 @@
 
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/ntc.h"

@@ -317,3 +317,18 @@ def test_epoch_permutation_epoch_parity(torch, split):
         o.epoch(0.2, seed=31 + e)
     for m in range(3):
         assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
+
+
+def test_light_rows_on_a_side_stream(torch):
+    """overlap = 1: light rows run on a second stream beside the split rows of
+    the same mode update; the result is the same as in stream order."""
+    p = small_zipf()
+    g, o = pair(p, torch, gparams=dict(SPLIT, overlap=1))
+    g2, _ = pair(p, torch, gparams=dict(SPLIT))
+    for e in range(2):
+        g.epoch(0.2, seed=61 + e)
+        g2.epoch(0.2, seed=61 + e)
+        o.epoch(0.2, seed=61 + e)
+    for m in range(3):
+        np.testing.assert_array_equal(g.get_factor(m), g2.get_factor(m))
+        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
