@@ -901,10 +901,12 @@ __global__ void __launch_bounds__(RowFinish<RP>::WARPS * 32) k_rows_finish(ModeA
 // ---------------------------------------------------------------------------
 // Heavy rows, step 1: per chunk of a row, keys of every position; positions
 // with key < lo are certainly in the sample and are written, in position
-// order; lo <= key < hi are
-// candidates whose fate depends on the whole row.  Each thread takes 8
-// consecutive positions per round, so one block scan serves 2048 positions.
-constexpr int kSamplePer = 8;
+// order; lo <= key < hi are candidates whose fate depends on the whole row.
+// Each thread takes 16 consecutive positions per round, so one block scan
+// serves 4096 positions (measured: 8 per thread 7.6, 16 per thread 7.1 ms per
+// epoch on the Zipf(1.1) 10^4-cube).
+constexpr int kSamplePer = 16;   // positions per thread per round of the split-row sampler
+constexpr int kResolvePer = 8;   // candidates per thread per round of the resolver's compaction
 
 // Keys of chunk `ch`: certain positions to a.vis[pb ...] in position order,
 // candidates to the chunk's candidate slots; returns the certain count (the
@@ -1051,19 +1053,19 @@ __global__ void __launch_bounds__(kThreads) k_heavy_resolve(ModeArgs a) {
         };
         const unsigned long long T = block_select_digit(get, ccap, m, digit, binmax, hist, mem, scan_tmp);
         int ne = 0;
-        for (int base = 0; base < ccap; base += kThreads * kSamplePer) {
-            const int j0 = base + threadIdx.x * kSamplePer;
-            unsigned long long cv[kSamplePer];
+        for (int base = 0; base < ccap; base += kThreads * kResolvePer) {
+            const int j0 = base + threadIdx.x * kResolvePer;
+            unsigned long long cv[kResolvePer];
             int nf = 0;
 #pragma unroll
-            for (int u = 0; u < kSamplePer; ++u) {
+            for (int u = 0; u < kResolvePer; ++u) {
                 cv[u] = j0 + u < ccap ? cand[j0 + u] : ~0ull;
                 nf += (cv[u] != ~0ull && cv[u] <= T) ? 1 : 0;
             }
             int tot;
             int off = ne + block_exclusive_scan(nf, scan_tmp, &tot);
 #pragma unroll
-            for (int u = 0; u < kSamplePer; ++u)
+            for (int u = 0; u < kResolvePer; ++u)
                 if (cv[u] != ~0ull && cv[u] <= T) a.extra[eoff + off++] = (uint32_t)(cv[u] & 0xFFFFFFFFull);
             ne += tot;
         }
