@@ -85,9 +85,11 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
  *   "heavy_rows"     rows with more than this many observations are split over
  *                    several thread blocks (default 4096, range 64..4096)
  *   "chunk"          observations per thread block of a split row (default 16384)
- *   "overlap"        1: rows that fit one block run on a second stream beside the
- *                    split rows of the same mode update (default 0; per-kernel
- *                    profile times then overlap)
+ *   "overlap"        2 (default): rows that fit one block run on a second stream
+ *                    beside the split rows' Gram of the same mode update (after
+ *                    their sampling); 1: beside the split rows' sampler; 0:
+ *                    stream order.  With 1 or 2 the per-kernel profile times of
+ *                    the light rows and the finish include concurrent work
  * Must be called before ntc_set_observed for "keep_perm".  Errors: NTC_ERR_ARG. */
 ntc_status ntc_set_param(ntc_handle* h, const char* key, double value);
 /* (also "profile": 1 brackets every mode-update kernel with CUDA events, see

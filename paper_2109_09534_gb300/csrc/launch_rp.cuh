@@ -23,27 +23,36 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         attr_err = e;
     });
     if (attr_err != cudaSuccess) return attr_err;
-    cudaError_t e = cudaSuccess;
     const bool fork = p.n_light > 0 && p.n_heavy > 0 && L.h->overlap;
-    if (fork) {
-        ntc_handle* h = L.h;
-        if (!h->side) {
-            if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return e;
-            if ((e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
-            if ((e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+    // light rows: in stream order, or on the side stream (forked here for
+    // overlap 1, beside the split-row sampler; after the sampler for overlap
+    // 2, beside the split-row Gram)
+    auto launch_light = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (fork) {
+            ntc_handle* h = L.h;
+            if (!h->side) {
+                if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+                if ((e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+                if ((e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+            }
+            if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
         }
-        if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
-    }
-    if (p.n_light > 0) {
-        const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv;
-        cudaStream_t ls = fork ? L.h->side : s;
-        e = L.run_on(ls, NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
-            k_light<RP, EW, BF, NOR><<<p.n_light, kLightThreads, LightSmem<RP, EW, BF, NOR>::bytes(a.n_other), ls>>>(a);
-        });
-        if (e != cudaSuccess) return e;
-        if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;
-    }
+        if (p.n_light > 0) {
+            const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv;
+            cudaStream_t ls = fork ? L.h->side : s;
+            e = L.run_on(ls, NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
+                k_light<RP, EW, BF, NOR><<<p.n_light, kLightThreads, LightSmem<RP, EW, BF, NOR>::bytes(a.n_other), ls>>>(a);
+            });
+            if (e != cudaSuccess) return e;
+            if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    const bool light_late = fork && L.h->overlap == 2;
+    if (!light_late && (e = launch_light()) != cudaSuccess) return e;
     if (p.n_heavy > 0 && a.perm) {
         // epoch-permutation variant: visits straight from the permutation
         e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_perm_visits<EW><<<p.n_chunks, kThreads, 0, s>>>(a); });
@@ -58,6 +67,7 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
             e = L.run(NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<EW><<<p.n_heavy, kThreads, 0, s>>>(a); });
             if (e != cudaSuccess) return e;
         }
+        if (light_late && (e = launch_light()) != cudaSuccess) return e;
         if (mask_only) {
             k_heavy_mask<EW><<<p.n_chunks + p.n_heavy, kThreads, 0, s>>>(a);
             ++*L.launches;

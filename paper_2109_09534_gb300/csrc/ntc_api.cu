@@ -791,7 +791,8 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
         if (!(v >= 0)) return fail(h, NTC_ERR_ARG, "init_seed must be >= 0");
         h->init_seed = (uint64_t)v;
     } else if (k == "overlap") {
-        h->overlap = v != 0.0;
+        if (v != 0.0 && v != 1.0 && v != 2.0) return fail(h, NTC_ERR_ARG, "overlap must be 0, 1 or 2");
+        h->overlap = (int)v;
     } else if (k == "profile") {
         h->profile = v != 0.0;
     } else if (k == "keep_perm") {

@@ -72,7 +72,7 @@ struct ntc_handle {
     cudaStream_t stream = nullptr;
     // light rows run on a side stream beside the split-row kernels of the same
     // mode update (they write disjoint rows); fork/join through two events
-    int overlap = 0;
+    int overlap = 2;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;

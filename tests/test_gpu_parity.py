@@ -319,12 +319,14 @@ def test_epoch_permutation_epoch_parity(torch, split):
         assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
 
 
-def test_light_rows_on_a_side_stream(torch):
-    """overlap = 1: light rows run on a second stream beside the split rows of
-    the same mode update; the result is the same as in stream order."""
+@pytest.mark.parametrize("overlap", [1, 2])
+def test_light_rows_on_a_side_stream(torch, overlap):
+    """overlap 1 / 2: light rows run on a second stream beside the split rows'
+    sampler / Gram of the same mode update; the result is the same as in
+    stream order."""
     p = small_zipf()
-    g, o = pair(p, torch, gparams=dict(SPLIT, overlap=1))
-    g2, _ = pair(p, torch, gparams=dict(SPLIT))
+    g, o = pair(p, torch, gparams=dict(SPLIT, overlap=overlap))
+    g2, _ = pair(p, torch, gparams=dict(SPLIT, overlap=0))
     for e in range(2):
         g.epoch(0.2, seed=61 + e)
         g2.epoch(0.2, seed=61 + e)
