@@ -393,9 +393,10 @@ def run_ntc(args):
             "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                             "share": v["ms"] / total_k if total_k else None} for k, v in prof.items()},
             "kernels_note": ("CUDA-event times per kernel class; light rows run on a second stream beside the "
-                             "split-row Gram, so the light and finish times include concurrent execution "
-                             "(the serialised shares are in the committed ncu launch list)") if args.overlap
-                            else "CUDA-event times per kernel class, stream order",
+                             "split-row Gram and the next update's split-row sampling on a third, so these "
+                             "times include concurrent execution (the serialised shares are in the committed "
+                             "ncu launch list)") if args.overlap else
+                            "CUDA-event times per kernel class; split-row sampling runs beside the Gram",
             "visits_per_s": ws * visits / (ms * 1e-3)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         del g

@@ -85,6 +85,10 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
  *   "heavy_rows"     rows with more than this many observations are split over
  *                    several thread blocks (default 4096, range 64..4096)
  *   "chunk"          observations per thread block of a split row (default 16384)
+ *   "pipeline"       1 (default): split-row sampling runs on its own stream with
+ *                    two scratch sets, so the next mode update's sampling runs
+ *                    beside this one's Gram (it needs no factors); 0: in stream
+ *                    order.  Set before ntc_set_observed (NTC_ERR_STATE after)
  *   "overlap"        2 (default): rows that fit one block run on a second stream
  *                    beside the split rows' Gram of the same mode update (after
  *                    their sampling); 1: beside the split rows' sampler; 0:

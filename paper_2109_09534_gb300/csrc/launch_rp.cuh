@@ -53,30 +53,54 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
     cudaError_t e = cudaSuccess;
     const bool light_late = fork && L.h->overlap == 2;
     if (!light_late && (e = launch_light()) != cudaSuccess) return e;
+    // split-row sampling: on the sampling stream when pipelined, so that it can
+    // run beside the previous update's Gram; its scratch set (a.sset) is free
+    // once the Gram two updates back has read it
+    ntc_handle* h = L.h;
+    const bool pipe = h->pipeline && p.n_heavy > 0;
+    cudaStream_t ss = s;
+    if (pipe) {
+        if (!h->samp) {
+            if ((e = cudaStreamCreateWithFlags(&h->samp, cudaStreamNonBlocking)) != cudaSuccess) return e;
+            for (int q = 0; q < 2; ++q) {
+                if ((e = cudaEventCreateWithFlags(&h->ev_sampled[q], cudaEventDisableTiming)) != cudaSuccess) return e;
+                if ((e = cudaEventCreateWithFlags(&h->ev_free[q], cudaEventDisableTiming)) != cudaSuccess) return e;
+            }
+        }
+        ss = h->samp;
+        if ((e = cudaStreamWaitEvent(ss, h->ev_free[a.sset], 0)) != cudaSuccess) return e;
+    }
     if (p.n_heavy > 0 && a.perm) {
         // epoch-permutation variant: visits straight from the permutation
-        e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_perm_visits<EW><<<p.n_chunks, kThreads, 0, s>>>(a); });
+        e = L.run_on(ss, NTC_K_HEAVY_SAMPLE, 0, [&] { k_perm_visits<EW><<<p.n_chunks, kThreads, 0, ss>>>(a); });
         if (e != cudaSuccess) return e;
     }
     if (p.n_heavy > 0) {
         if (!a.perm) {
-            e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, s);
+            e = cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * p.n_heavy, ss);
             if (e != cudaSuccess) return e;
-            e = L.run(NTC_K_HEAVY_SAMPLE, 0, [&] { k_heavy_sample<EW><<<p.n_chunks, kThreads, 0, s>>>(a); });
+            e = L.run_on(ss, NTC_K_HEAVY_SAMPLE, 0, [&] { k_heavy_sample<EW><<<p.n_chunks, kThreads, 0, ss>>>(a); });
             if (e != cudaSuccess) return e;
-            e = L.run(NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<EW><<<p.n_heavy, kThreads, 0, s>>>(a); });
+            e = L.run_on(ss, NTC_K_HEAVY_RESOLVE, 0, [&] { k_heavy_resolve<EW><<<p.n_heavy, kThreads, 0, ss>>>(a); });
             if (e != cudaSuccess) return e;
+        }
+        if (pipe) {
+            if ((e = cudaEventRecord(h->ev_sampled[a.sset], ss)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, h->ev_sampled[a.sset], 0)) != cudaSuccess) return e;
         }
         if (light_late && (e = launch_light()) != cudaSuccess) return e;
         if (mask_only) {
             k_heavy_mask<EW><<<p.n_chunks + p.n_heavy, kThreads, 0, s>>>(a);
             ++*L.launches;
+            if (pipe && (e = cudaEventRecord(h->ev_free[a.sset], s)) != cudaSuccess) return e;
         } else {
             e = L.run(NTC_K_HEAVY_GRAM, p.visits_heavy * L.bpv, [&] {
                 k_heavy_gram<RP, EW, BF, NOR><<<p.n_chunks + p.n_heavy, GramNT<RP>::value,
                                            HeavyGramSmem<RP, EW, BF, NOR>::bytes(a.n_other), s>>>(a);
             });
             if (e != cudaSuccess) return e;
+            // the Gram was the last reader of this sampling set
+            if (pipe && (e = cudaEventRecord(h->ev_free[a.sset], s)) != cudaSuccess) return e;
             e = L.run(NTC_K_FINISH, 0, [&] {
                 k_heavy_reduce<RP><<<p.n_groups, kThreads, 0, s>>>(a);
                 k_heavy_rowsum<RP><<<p.n_heavy, kThreads, 0, s>>>(a);

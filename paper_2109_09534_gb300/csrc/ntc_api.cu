@@ -180,13 +180,15 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     p.cand_total = cand_total;
     p.extra_total = extra_total;
     // scratch sized for this plan
-    NTC_CUDA(h, h->vis.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(h->nnz, 1)));
-    NTC_CUDA(h, h->vis_cnt.ensure(sizeof(uint32_t) * (size_t)std::max(p.n_chunks, 1)));
-    NTC_CUDA(h, h->cand_cnt.ensure(sizeof(uint32_t) * (size_t)std::max(p.n_chunks, 1)));
-    NTC_CUDA(h, h->cand.ensure(sizeof(unsigned long long) * (size_t)std::max<int64_t>(cand_total, 1)));
-    NTC_CUDA(h, h->extra.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(extra_total, 1)));
-    NTC_CUDA(h, h->extra_cnt.ensure(sizeof(uint32_t) * (size_t)std::max(p.n_heavy, 1)));
-    NTC_CUDA(h, h->flags.ensure(sizeof(uint32_t) * (size_t)std::max(p.n_heavy, 1)));
+    for (int b = 0; b < (h->pipeline ? 2 : 1); ++b) {
+        NTC_CUDA(h, h->vis[b].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(h->nnz, 1)));
+        NTC_CUDA(h, h->vis_cnt[b].ensure(sizeof(uint32_t) * (size_t)std::max(p.n_chunks, 1)));
+        NTC_CUDA(h, h->cand_cnt[b].ensure(sizeof(uint32_t) * (size_t)std::max(p.n_chunks, 1)));
+        NTC_CUDA(h, h->cand[b].ensure(sizeof(unsigned long long) * (size_t)std::max<int64_t>(cand_total, 1)));
+        NTC_CUDA(h, h->extra[b].ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(extra_total, 1)));
+        NTC_CUDA(h, h->extra_cnt[b].ensure(sizeof(uint32_t) * (size_t)std::max(p.n_heavy, 1)));
+        NTC_CUDA(h, h->flags[b].ensure(sizeof(uint32_t) * (size_t)std::max(p.n_heavy, 1)));
+    }
     NTC_CUDA(h, h->partial.ensure(sizeof(float) * (size_t)partial_width(h->rp) *
                                   (size_t)std::max(p.n_chunks + p.n_heavy, 1)));
     NTC_CUDA(h, h->partial2.ensure(sizeof(float) * (size_t)partial_width(h->rp) * (size_t)std::max(p.n_groups, 1)));
@@ -237,13 +239,15 @@ ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t a
     a.heavy_cand = p.heavy_cand.as<int4>();
     a.n_chunks = p.n_chunks;
     a.n_heavy = p.n_heavy;
-    a.vis = h->vis.as<uint32_t>();
-    a.vis_cnt = h->vis_cnt.as<uint32_t>();
-    a.cand = h->cand.as<unsigned long long>();
-    a.cand_cnt = h->cand_cnt.as<uint32_t>();
-    a.extra = h->extra.as<uint32_t>();
-    a.extra_cnt = h->extra_cnt.as<uint32_t>();
-    a.flags = h->flags.as<uint32_t>();
+    const int sb = h->pipeline ? (int)(h->upd & 1) : 0;   // sampling set of this update
+    a.vis = h->vis[sb].as<uint32_t>();
+    a.vis_cnt = h->vis_cnt[sb].as<uint32_t>();
+    a.cand = h->cand[sb].as<unsigned long long>();
+    a.cand_cnt = h->cand_cnt[sb].as<uint32_t>();
+    a.extra = h->extra[sb].as<uint32_t>();
+    a.extra_cnt = h->extra_cnt[sb].as<uint32_t>();
+    a.flags = h->flags[sb].as<uint32_t>();
+    a.sset = sb;
     a.partial = h->partial.as<float>();
     a.groups = p.groups.as<int4>();
     a.heavy_groups = p.heavy_groups.as<int2>();
@@ -300,6 +304,7 @@ ntc_status run_snmc(ntc_handle* h, int mode, double c, uint64_t seed, uint64_t a
         a.vwarm = h->power_warm ? h->vwarm[mode].as<float>() : nullptr;
         set_perm(h, a, p, c, ao_iter, l);
         NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, p, L, false));
+        h->upd += 1;
         h->stats.visits += p.visits;
         h->stats.visits_heavy += p.visits_heavy;
         h->stats.rows_updated += p.rows_updated;
@@ -676,9 +681,11 @@ int64_t handle_device_bytes(const ntc_handle* h) {
         b += (int64_t)(p.light_rows.bytes + p.light_k.bytes + p.chunks.bytes + p.chunk_caps.bytes + p.heavy.bytes +
                        p.bracket.bytes + p.heavy_cand.bytes + p.groups.bytes + p.heavy_groups.bytes);
     }
-    b += (int64_t)(h->Y.bytes + h->coo_idx.bytes + h->coo_val.bytes + h->dims_dev.bytes + h->vis.bytes +
-                   h->vis_cnt.bytes + h->cand.bytes + h->cand_cnt.bytes + h->extra.bytes + h->extra_cnt.bytes +
-                   h->flags.bytes + h->partial.bytes + h->partial2.bytes + h->row_sum.bytes + h->stat.bytes +
+    for (int q = 0; q < 2; ++q)
+        b += (int64_t)(h->vis[q].bytes + h->vis_cnt[q].bytes + h->cand[q].bytes + h->cand_cnt[q].bytes +
+                       h->extra[q].bytes + h->extra_cnt[q].bytes + h->flags[q].bytes);
+    b += (int64_t)(h->Y.bytes + h->coo_idx.bytes + h->coo_val.bytes + h->dims_dev.bytes +
+                   h->partial.bytes + h->partial2.bytes + h->row_sum.bytes + h->stat.bytes +
                    h->red.bytes + h->mask.bytes + h->stage_idx.bytes + h->stage_val.bytes + h->sort_k0.bytes +
                    h->sort_k1.bytes + h->sort_v0.bytes + h->sort_v1.bytes + h->sort_hist.bytes + h->sort_sums.bytes +
                    h->bad_flag.bytes + h->row_cnt.bytes + h->entry_tmp.bytes);
@@ -797,6 +804,9 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
         h->profile = v != 0.0;
     } else if (k == "keep_perm") {
         h->keep_perm = v != 0.0;
+    } else if (k == "pipeline") {
+        if (h->nnz >= 0) return fail(h, NTC_ERR_STATE, "pipeline must be set before ntc_set_observed");
+        h->pipeline = v != 0.0 ? 1 : 0;
     } else if (k == "power_warm") {
         h->power_warm = v != 0.0 ? 1 : 0;
     } else if (k == "sampler") {
@@ -1041,6 +1051,7 @@ ntc_status ntc_sample_mask(ntc_handle* h, int mode, double c, uint64_t seed, uin
     set_perm(h, a, h->plan[mode], c, ao_iter, inner);
     Launcher L = make_launcher(h);
     NTC_CUDA(h, launch_mode(h->rp, ew_of(h->order), h->storage_bf16 != 0, a, h->plan[mode], L, true));
+    h->upd += 1;
     NTC_CUDA(h, cudaMemcpyAsync(mask, h->mask.p, (size_t)h->nnz, cudaMemcpyDeviceToHost, h->stream));
     NTC_CUDA(h, cudaStreamSynchronize(h->stream));
     return NTC_OK;

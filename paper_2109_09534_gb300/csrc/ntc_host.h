@@ -95,8 +95,15 @@ struct ntc_handle {
     std::vector<int64_t> row_ptr_h[ntc::kMaxOrder];
     ntc::ModePlan plan[ntc::kMaxOrder];
     // scratch
-    ntc::DevMem vis, vis_cnt, cand, cand_cnt, extra, extra_cnt, flags, partial, partial2, row_sum, stat, red,
-        mask;
+    // split-row sampling scratch, two sets: update u uses set u % 2, so the
+    // sampling of the next mode update can run while this one's Gram reads
+    // its lists ("pipeline")
+    ntc::DevMem vis[2], vis_cnt[2], cand[2], cand_cnt[2], extra[2], extra_cnt[2], flags[2];
+    ntc::DevMem partial, partial2, row_sum, stat, red, mask;
+    int pipeline = 1;
+    uint64_t upd = 0;                       // mode updates launched so far
+    cudaStream_t samp = nullptr;            // split-row sampling stream
+    cudaEvent_t ev_sampled[2] = {}, ev_free[2] = {};
     // ntc_set_observed staging (the next COO) and radix-sort buffers, kept
     // between calls unless "cache_staging" is 0
     int cache_staging = 1;
@@ -125,6 +132,11 @@ struct ntc_handle {
         if (side) cudaStreamDestroy(side);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        for (int b = 0; b < 2; ++b) {
+            if (ev_sampled[b]) cudaEventDestroy(ev_sampled[b]);
+            if (ev_free[b]) cudaEventDestroy(ev_free[b]);
+        }
+        if (samp) cudaStreamDestroy(samp);
     }
 };
 

@@ -286,6 +286,7 @@ struct ModeArgs {
     // epoch-permutation sampling variant: slot perm_slot of epoch perm_epoch;
     // split rows' visits are stored from the row's start, chunk c's at vis_off[c]
     int perm;
+    int sset;                 // sampling scratch set of this update (0 or 1)
     uint32_t perm_epoch;
     int64_t perm_slot;
     const int32_t* vis_off;

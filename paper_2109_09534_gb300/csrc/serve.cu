@@ -89,8 +89,8 @@ int64_t model_bytes(const ntc_job_desc* d) {
     b += sum_dims * 8;                                        // row maps
     b += sum_dims * rp * (4 + (d->storage_bf16 ? 2 : 0));    // masters (+ BF16 copies)
     b += sum_dims * 8;                                        // light-row plans
-    b += nnz * 4;                                             // visit lists
-    b += nnz + (1 << 20);                                     // candidates and chosen lists
+    b += 2 * nnz * 4;                                         // visit lists (two sampling sets)
+    b += 2 * (nnz + (1 << 20));                               // candidates and chosen lists (two sets)
     const int64_t items = nnz / 16384 + 2 * max_dim + 1;      // chunks + split rows (bound)
     b += items * pw * 4 * 2;                                  // partials and group sums
     b += max_dim * pw * 4;                                    // per-row reduced sums
