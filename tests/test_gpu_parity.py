@@ -334,3 +334,23 @@ def test_light_rows_on_a_side_stream(torch, overlap):
     for m in range(3):
         np.testing.assert_array_equal(g.get_factor(m), g2.get_factor(m))
         assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
+
+
+def test_pipelined_sampling_matches_stream_order(torch):
+    """pipeline = 1 (default): the next update's split-row sampling runs on its
+    own stream with a second scratch set; results equal stream order bit for
+    bit, also with the permutation sampler and after a change of c."""
+    p = small_zipf()
+    for extra in (dict(), dict(sampler=1)):
+        a, _ = pair(p, torch, gparams=dict(SPLIT, **extra))
+        b, _ = pair(p, torch, gparams=dict(SPLIT, pipeline=0, overlap=0, **extra))
+        for c, seed in ((0.2, 71), (0.1, 72), (0.2, 73)):
+            a.epoch(c, seed=seed)
+            b.epoch(c, seed=seed)
+        for m in range(3):
+            np.testing.assert_array_equal(a.get_factor(m), b.get_factor(m))
+    g = ntc.NTC(p.dims, p.rank, p.lam, stream=torch.cuda.current_stream().cuda_stream)
+    g.set_observed(p.idx_train, p.val_train)
+    with pytest.raises(ntc.NTCError) as e:
+        g.set_param("pipeline", 0)
+    assert e.value.status == ntc.NTC_ERR_STATE
