@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "observed entries/s per AO epoch"
 UNIT = "entries/s"
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 
 
 def parse():
@@ -47,6 +48,9 @@ def parse():
     ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2],
                     help="light rows on a second stream: 2 beside the split-row Gram (default), 1 beside the "
                          "sampler, 0 stream order")
+    ap.add_argument("--gram-tc", type=int, default=1, choices=[0, 1],
+                    help="1: split-row Gram on the tensor cores where the shape has a kernel (R_pad = 32, "
+                         "orders 2-4; default); 0: FP32 FMA")
     ap.add_argument("--sampler", default="independent", choices=["independent", "perm"],
                     help="perm: epoch-permutation minibatches (labelled variant)")
     ap.add_argument("--power-warm", type=int, default=0,
@@ -95,6 +99,8 @@ def config(p, args):
         text += f", variant: warm-started power method, {args.power_warm} iterations"
     if getattr(args, "overlap", 2) == 0:
         text += ", light rows in stream order"
+    if getattr(args, "gram_tc", 1) == 0:
+        text += ", split-row Gram on FP32 FMA"
     if getattr(args, "sampler", "independent") == "perm":
         text += ", variant: epoch-permutation minibatches (disjoint stretches of one permutation per row and epoch)"
     return {"workload": text, "dims": p.dims, "rank": p.rank, "nnz_train": p.nnz, "c": p.c, "lambda": p.lam,
@@ -110,9 +116,21 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# nominal dense TF32 / BF16 tensor rates of the part (1.1 and 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak():
+    """TF32 dense peak in TFLOP/s: the measured bf16 GEMM burst times the nominal ratio."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["bf16_tflops"]) * TF32_PER_BF16, "measured bf16 burst x 1.1/2.25"
+    return FALLBACK_BF16_TFLOPS * TF32_PER_BF16, "fallback bf16 x 1.1/2.25"
+
+
 # sources of the epoch kernels (the serving runtime and the host API are not
 # part of what the DRAM counters measured)
-KERNEL_SOURCES = ("ntc_internal.cuh", "nmc_kernels.cuh", "launch_rp.cuh",
+KERNEL_SOURCES = ("ntc_internal.cuh", "nmc_kernels.cuh", "gram_tc.cuh", "launch_rp.cuh",
                   "nmc_rp8.cu", "nmc_rp16.cu", "nmc_rp32.cu", "nmc_rp64.cu")
 
 
@@ -288,7 +306,7 @@ def run_ntc(args):
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
     p = workload(args)
-    params = dict(profile=1, overlap=args.overlap)
+    params = dict(profile=1, overlap=args.overlap, gram_tc=args.gram_tc)
     if args.storage_bf16:
         params["storage_bf16"] = 1
     if args.power_warm:
@@ -343,14 +361,33 @@ def run_ntc(args):
     per_launch_ms = d["ms"] / max(d["launches"], 1)
     bytes_per_launch = d["alg_bytes"] / max(d["launches"], 1)
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
-    kname = {"light": "k_light", "heavy_sample": "k_heavy_sample", "heavy_resolve": "k_heavy_resolve",
-             "heavy_gram": "k_heavy_gram", "finish": "k_rows_finish"}[dom]
-    total_k = sum(v["ms"] for v in prof.values())
     R, N = p.rank, p.order
+    # the tensor-core Gram runs at padded rank 32 (16 < R <= 32) and orders 2-4
+    tensor_gram = bool(args.gram_tc) and 16 < R <= 32 and N <= 4
+    gram_name = "k_heavy_gram_tc" if tensor_gram else "k_heavy_gram"
+    kname = {"light": "k_light", "heavy_sample": "k_heavy_sample", "heavy_resolve": "k_heavy_resolve",
+             "heavy_gram": gram_name, "finish": "k_rows_finish"}[dom]
+    total_k = sum(v["ms"] for v in prof.values())
     flops_per_visit = (N - 2) * R + 2 * R + R * (R + 1)
     s_bytes = 2 if args.storage_bf16 else 4
-    gram_flops = prof["heavy_gram"]["alg_bytes"] // ((N - 1) * 4 + 4 + (N - 1) * R * s_bytes) * flops_per_visit
-    gram_tf = gram_flops / (prof["heavy_gram"]["ms"] * 1e-3) / 1e12 if prof["heavy_gram"]["ms"] > 0 else 0.0
+    gram_visits = prof["heavy_gram"]["alg_bytes"] // ((N - 1) * 4 + 4 + (N - 1) * R * s_bytes)
+    gram_s = prof["heavy_gram"]["ms"] * 1e-3
+    gram_tf = gram_visits * flops_per_visit / gram_s / 1e12 if gram_s > 0 else 0.0
+    if tensor_gram:
+        # issued tensor work: one M=128 x N=32 x K=8 TF32 MMA per 8 visits
+        tc_flops_per_visit = 2 * 128 * 32
+        tc_tf = gram_visits * tc_flops_per_visit / gram_s / 1e12 if gram_s > 0 else 0.0
+        tpk, tpk_kind = tf32_peak()
+        compute_roof = {"roofline_tensor": {
+            "kernel": gram_name, "achieved": tc_tf, "peak": tpk, "unit": "TFLOP/s", "frac": tc_tf / tpk,
+            "peak_kind": tpk_kind, "dtype": "tf32 (3xTF32 split of FP32)",
+            "flops_per_visit_issued": tc_flops_per_visit, "alg_flops_per_visit": flops_per_visit,
+            "alg_tflops": gram_tf}}
+    else:
+        compute_roof = {"roofline_alu": {
+            "kernel": gram_name, "achieved": gram_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": gram_tf / fp32_peak if fp32_peak else None,
+            "peak_kind": "measured FP32 FMA microbenchmark, same run", "flops_per_visit": flops_per_visit}}
 
     # end to end through the C ABI with pinned host buffers
     idx_pin = torch.from_numpy(np.ascontiguousarray(p.idx_train)).pin_memory()
@@ -386,10 +423,7 @@ def run_ntc(args):
             "roofline_epoch": {"alg_bytes_per_epoch": alg_bytes / args.steps,
                                "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9 * ws,
                                "frac_of_hbm": alg_bytes / (ms * 1e-3) / 1e9 / hbm, "peak_kind": hbm_kind},
-            "roofline_alu": {"kernel": "k_heavy_gram", "achieved": gram_tf, "peak": fp32_peak,
-                             "unit": "TFLOP/s", "frac": gram_tf / fp32_peak if fp32_peak else None,
-                             "peak_kind": "measured FP32 FMA microbenchmark, same run",
-                             "flops_per_visit": flops_per_visit},
+            **compute_roof,
             "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                             "share": v["ms"] / total_k if total_k else None} for k, v in prof.items()},
             "kernels_note": ("CUDA-event times per kernel class; light rows run on a second stream beside the "

@@ -89,6 +89,10 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
  *                    two scratch sets, so the next mode update's sampling runs
  *                    beside this one's Gram (it needs no factors); 0: in stream
  *                    order.  Set before ntc_set_observed (NTC_ERR_STATE after)
+ *   "gram_tc"        1 (default): at padded rank 32 and orders 2-4 the split rows'
+ *                    Gram G = sum k k^T runs on the tensor cores (TF32 operands
+ *                    split into big + small parts for FP32 accuracy); 0: FP32
+ *                    FMA.  Other shapes always use FP32 FMA
  *   "overlap"        2 (default): rows that fit one block run on a second stream
  *                    beside the split rows' Gram of the same mode update (after
  *                    their sampling); 1: beside the split rows' sampler; 0:
@@ -160,8 +164,10 @@ ntc_status ntc_sync(ntc_handle* h);
  * floor(c n_p) (the sampled observations), the part of them in rows split over
  * several blocks, rows updated, rows skipped (floor(c n_p) = 0), rows that used
  * the exact fallback selector, the algorithmic bytes moved (index, value and
- * factor-row reads per visit, factor-row reads/writes per row update) and the
- * number of kernel launches enqueued. */
+ * factor-row reads per visit, factor-row reads/writes per row update), the
+ * number of kernel launches enqueued, and the number of tensor-core Gram blocks
+ * whose bounded wait for their MMAs gave up (0 unless the device misbehaved;
+ * their partial sums are then not valid). */
 typedef struct {
     int64_t visits;
     int64_t visits_heavy;
@@ -170,6 +176,7 @@ typedef struct {
     int64_t fallback_rows;
     int64_t alg_bytes;
     int64_t kernel_launches;
+    int64_t wait_timeouts;
 } ntc_stats;
 ntc_status ntc_get_stats(ntc_handle* h, ntc_stats* out);
 

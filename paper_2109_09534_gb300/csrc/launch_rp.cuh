@@ -4,10 +4,20 @@
 // nmc_rp*.cu so that the instantiations compile in parallel.
 #pragma once
 
+#include "gram_tc.cuh"
 #include "nmc_kernels.cuh"
 #include "ntc_host.h"
 
 namespace ntc {
+
+// The split-row Gram runs on the tensor cores (gram_tc.cuh) at padded rank
+// 32 with the other modes' count fixed at compile time (orders 2-4), unless
+// the handle's "gram_tc" is 0; visits per staged tile:
+template <int RP, int EW, int NOR>
+constexpr bool kTensorGram = RP == 32 && EW == 4 && NOR > 0;
+constexpr int kTcTile = 64;
+constexpr int kTcWindow = 1;   // tiles per tensor-memory accumulation window
+constexpr int kTcThreads = 128;
 
 template <int RP, int EW, bool BF, int NOR>
 cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, bool mask_only) {
@@ -20,6 +30,8 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         cudaError_t e = set_smem(k_light<RP, EW, BF, NOR>, LightSmem<RP, EW, BF, NOR>::bytes(nomax));
         if (e == cudaSuccess) e = set_smem(k_heavy_gram<RP, EW, BF, NOR>, HeavyGramSmem<RP, EW, BF, NOR>::bytes(nomax));
         if (e == cudaSuccess) e = set_smem(k_rows_finish<RP>, RowFinish<RP>::bytes());
+        if constexpr (kTensorGram<RP, EW, NOR>)
+            if (e == cudaSuccess) e = set_smem(k_heavy_gram_tc<EW, BF, NOR, kTcTile, kTcWindow, kTcThreads>, GramTC<EW, kTcTile, kTcWindow, kTcThreads>::BYTES);
         attr_err = e;
     });
     if (attr_err != cudaSuccess) return attr_err;
@@ -95,8 +107,17 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
             if (pipe && (e = cudaEventRecord(h->ev_free[a.sset], s)) != cudaSuccess) return e;
         } else {
             e = L.run(NTC_K_HEAVY_GRAM, p.visits_heavy * L.bpv, [&] {
-                k_heavy_gram<RP, EW, BF, NOR><<<p.n_chunks + p.n_heavy, GramNT<RP>::value,
-                                           HeavyGramSmem<RP, EW, BF, NOR>::bytes(a.n_other), s>>>(a);
+                bool tensor = false;
+                if constexpr (kTensorGram<RP, EW, NOR>) {
+                    if (h->gram_tc) {
+                        using T = GramTC<EW, kTcTile, kTcWindow, kTcThreads>;
+                        k_heavy_gram_tc<EW, BF, NOR, kTcTile, kTcWindow, kTcThreads><<<p.n_chunks + p.n_heavy, T::NT, T::BYTES, s>>>(a);
+                        tensor = true;
+                    }
+                }
+                if (!tensor)
+                    k_heavy_gram<RP, EW, BF, NOR><<<p.n_chunks + p.n_heavy, GramNT<RP>::value,
+                                               HeavyGramSmem<RP, EW, BF, NOR>::bytes(a.n_other), s>>>(a);
             });
             if (e != cudaSuccess) return e;
             // the Gram was the last reader of this sampling set

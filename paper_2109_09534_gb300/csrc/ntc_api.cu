@@ -256,6 +256,7 @@ ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t a
     a.row_sum = h->row_sum.as<float>();
     a.n_light = p.n_light;
     a.stat_fallback = h->stat.as<unsigned long long>();
+    a.stat_wait = h->stat.as<unsigned long long>() + 1;
     a.mask_out = nullptr;
     return a;
 }
@@ -322,8 +323,8 @@ ntc_status check_ready(ntc_handle* h) {
 
 ntc_status reset_stats(ntc_handle* h) {
     h->stats = ntc_stats{};
-    NTC_CUDA(h, h->stat.ensure(sizeof(unsigned long long)));
-    NTC_CUDA(h, cudaMemsetAsync(h->stat.p, 0, sizeof(unsigned long long), h->stream));
+    NTC_CUDA(h, h->stat.ensure(2 * sizeof(unsigned long long)));
+    NTC_CUDA(h, cudaMemsetAsync(h->stat.p, 0, 2 * sizeof(unsigned long long), h->stream));
     return NTC_OK;
 }
 
@@ -812,6 +813,8 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
     } else if (k == "sampler") {
         if (v != 0.0 && v != 1.0) return fail(h, NTC_ERR_ARG, "sampler must be 0 (independent) or 1 (epoch permutation)");
         h->sampler = (int)v;
+    } else if (k == "gram_tc") {
+        h->gram_tc = v != 0.0 ? 1 : 0;
     } else if (k == "cache_staging") {
         h->cache_staging = v != 0.0 ? 1 : 0;
     } else if (k == "bracket_z") {
@@ -1010,10 +1013,11 @@ ntc_status ntc_get_stats(ntc_handle* h, ntc_stats* out) {
     if (!h || !out) return NTC_ERR_ARG;
     *out = h->stats;
     if (h->stat.p) {
-        unsigned long long fb = 0;
-        NTC_CUDA(h, cudaMemcpyAsync(&fb, h->stat.p, sizeof(fb), cudaMemcpyDeviceToHost, h->stream));
+        unsigned long long st[2] = {0, 0};
+        NTC_CUDA(h, cudaMemcpyAsync(st, h->stat.p, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
         NTC_CUDA(h, cudaStreamSynchronize(h->stream));
-        out->fallback_rows = (int64_t)fb;
+        out->fallback_rows = (int64_t)st[0];
+        out->wait_timeouts = (int64_t)st[1];
     }
     return NTC_OK;
 }

@@ -101,6 +101,7 @@ struct ntc_handle {
     ntc::DevMem vis[2], vis_cnt[2], cand[2], cand_cnt[2], extra[2], extra_cnt[2], flags[2];
     ntc::DevMem partial, partial2, row_sum, stat, red, mask;
     int pipeline = 1;
+    int gram_tc = 1;         // split-row Gram on the tensor cores where a kernel exists (R_pad 32, orders 2-4)
     uint64_t upd = 0;                       // mode updates launched so far
     cudaStream_t samp = nullptr;            // split-row sampling stream
     cudaEvent_t ev_sampled[2] = {}, ev_free[2] = {};

@@ -292,6 +292,7 @@ struct ModeArgs {
     const int32_t* vis_off;
     int n_light;
     unsigned long long* stat_fallback;  // counter of rows that used the exact selector
+    unsigned long long* stat_wait;      // counter of tensor-core waits that timed out
     uint8_t* mask_out;        // sampler-only mode: mask over bucket positions
 };
 

@@ -38,7 +38,7 @@ class ntc_stats(ctypes.Structure):
     _fields_ = [("visits", ctypes.c_int64), ("visits_heavy", ctypes.c_int64),
                 ("rows_updated", ctypes.c_int64), ("rows_skipped", ctypes.c_int64),
                 ("fallback_rows", ctypes.c_int64), ("alg_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("wait_timeouts", ctypes.c_int64)]
 
 
 class ntc_job_desc(ctypes.Structure):

@@ -1,0 +1,89 @@
+"""GPU parity of the tensor-core split-row Gram (tcgen05, TF32 operands split
+into big + small parts) at padded rank 32, orders 2-4: one mode update (Alg. 1)
+and one epoch against the FP64 oracle, and against the FP32 FMA Gram of the
+same handle ("gram_tc" 0).  Ragged tiles, rank padding (R < 32), many tiles
+per block and zero-visit blocks all occur in these cases."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_09534_gb300 import synth
+
+from gpu_helpers import pair, rel_err, require_gpu, small_zipf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_gpu()
+
+
+CASES = {
+    "order2_r32": lambda: synth.make_problem([400, 250], 32, 60_000, index_dist="zipf", sigma=0.01,
+                                             test_frac=0.05, seed=21),
+    "zipf2k_r32": lambda: small_zipf(),
+    "zipf2k_r29": lambda: small_zipf(rank=29),
+    "order4_r32": lambda: synth.make_problem([120, 90, 40, 30], 32, 120_000, index_dist="zipf", sigma=0.01,
+                                             test_frac=0.05, seed=22),
+}
+# split thresholds: small chunks (ragged tiles, many blocks, some with no visits)
+# and the default chunk (about 1600 visits, 26 tiles per block, at c = 0.1)
+SPLITS = {"small": dict(heavy_rows=128, chunk=700), "default": dict(heavy_rows=128)}
+
+
+def one_update(p, torch, gram_tc, split, c=0.1, bf16=False):
+    g, o = pair(p, torch, gparams=dict(SPLITS[split], gram_tc=gram_tc, storage_bf16=int(bf16)))
+    out = []
+    for m in range(p.order):
+        g.ao_iter = 2
+        o.ao_iter = 2
+        g.snmc(m, c, seed=77)
+        o.snmc(m, c, seed=77)
+        out.append((g.get_factor(m), o.get_factor(m)))
+    st = g.stats()
+    return out, st
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("split", list(SPLITS))
+def test_single_update_tensor_gram(torch, case, split):
+    """FP32 factors after one mode update: tensor-core Gram vs FP64 within 1e-6."""
+    p = CASES[case]()
+    got, st = one_update(p, torch, 1, split)
+    assert st["visits_heavy"] > 0 and st["wait_timeouts"] == 0
+    for m, (a, want) in enumerate(got):
+        assert rel_err(a, want) <= 1e-6, (case, split, m, rel_err(a, want))
+
+
+@pytest.mark.parametrize("case", ["zipf2k_r32", "order4_r32"])
+def test_tensor_gram_matches_fma_gram(torch, case):
+    """The two Gram paths of one handle agree to FP32 rounding."""
+    p = CASES[case]()
+    tc, _ = one_update(p, torch, 1, "small")
+    fma, _ = one_update(p, torch, 0, "small")
+    for m in range(p.order):
+        assert rel_err(tc[m][0], fma[m][0]) <= 1e-6, m
+
+
+def test_tensor_gram_bf16_storage(torch):
+    p = CASES["zipf2k_r32"]()
+    tc, st = one_update(p, torch, 1, "small", bf16=True)
+    fma, _ = one_update(p, torch, 0, "small", bf16=True)
+    assert st["wait_timeouts"] == 0
+    for m in range(p.order):
+        assert rel_err(tc[m][0], tc[m][1]) <= 2e-2, m
+        assert rel_err(tc[m][0], fma[m][0]) <= 1e-6, m
+
+
+@pytest.mark.parametrize("c", [0.1, 1.0])
+def test_epoch_tensor_gram(torch, c):
+    """One epoch at c = 0.1 (10 AO iterations) and one full-gradient AO
+    iteration at c = 1 (every visit of a split row, the longest blocks)."""
+    p = small_zipf()
+    g, o = pair(p, torch, gparams=dict(heavy_rows=128, gram_tc=1))
+    g.epoch(c, seed=5)
+    o.epoch(c, seed=5)
+    for m in range(3):
+        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
+    assert g.stats()["wait_timeouts"] == 0
