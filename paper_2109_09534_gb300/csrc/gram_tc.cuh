@@ -147,8 +147,10 @@ struct GramTC {
     static constexpr int RP = 32;
     static constexpr int NT = NT_;                // threads: 128 or 256
     static constexpr int BLOCKS = NT == 128 ? 4 : 3;   // resident blocks per SM (registers)
-    // D rows 0..2R-1 live in TMEM lanes 0..63, which warps w with w % 4 < 2
-    // read; with 8 warps, warps w and w + 4 take 16 columns each
+    // D's 2R useful rows sit in TMEM lanes 0..63 for even tiles and, with A's
+    // descriptor started 8 row groups early, in lanes 64..127 for odd tiles:
+    // warps w with (w % 4) / 2 equal to the tile's parity fold it (with 8
+    // warps, w and w + 4 take 16 columns each), so the folding alternates
     static constexpr int FCOLS = RP / (NT / 128);
     static constexpr int SPV = RP / 8;            // product slots per visit: 8 ranks each
     static constexpr int RS = VT * SPV / NT;      // product slots per thread and tile
@@ -167,8 +169,10 @@ struct GramTC {
     static constexpr int SE = 5;                  // entry stages
     static constexpr int ENTB = EW * 4;
     static constexpr int PW = 10 * 64 + RP;       // partial: ten 8x8 upper tiles, then b
-    // shared memory: [mbarriers, TMEM slot][S0][S1][entries][reach pad]
+    // shared memory: [mbarriers, TMEM slot][S0][S1][entries][reach pad]; odd
+    // tiles (always S1) start A's reads 8 SBO early, inside S0
     static constexpr int S_OFF = 64;
+    static_assert(8 * SBO <= SB, "odd tiles' shifted A reads stay inside S0");
     static constexpr int E_OFF = S_OFF + 2 * SB;
     static constexpr int USED = E_OFF + SE * VT * ENTB;
     // Furthest byte an operand read of the last K step of S1 can touch (16 row
@@ -176,13 +180,13 @@ struct GramTC {
     static constexpr int LAST = S_OFF + SB + (VT / 4 - 2) * KGB;
     static constexpr int REACH = LAST + 15 * SBO + KGB + 128;
     static constexpr int BYTES = ((USED > REACH ? USED : REACH) + 127) / 128 * 128;
-    // epilogue buffers alias S0 once every MMA has completed: bb and sb sums
-    // [RP][RP + 1], then the b partials [NT][8]
+    // epilogue buffers alias S0 and S1 once every MMA has completed: bb and sb
+    // sums of even and odd tiles [4][RP][RP + 1], then the b partials [NT][8]
     static constexpr int TSTR = RP + 1;
     static_assert(VT % 8 == 0 && VT <= NT && (VT * SPV) % NT == 0 && NT % SPV == 0, "tile shape");
     static_assert(FW >= 1, "window");
     static_assert(NT == 128 || NT == 256, "block");
-    static_assert(2 * RP * TSTR * 4 + NT * 32 <= SB, "epilogue fits in S0");
+    static_assert(4 * RP * TSTR * 4 + NT * 32 <= 2 * SB, "epilogue fits in S0 and S1");
     static_assert(SBO % 16 == 0 && KGB % 16 == 0, "descriptor offsets are 16-byte multiples");
     static_assert(EW == 4, "orders 2-4");
 };
@@ -291,8 +295,9 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
             }
         }
     };
-    // folding warps: lane block (warp % 4) of D, columns (warp / 4) FC ..
-    const bool folder = (warp & 3) < 2;
+    // folding warps of tiles of parity fpar: lane block (warp % 4) of D,
+    // columns (warp / 4) FC ..
+    const int fpar = (warp & 3) >> 1;
     const uint32_t fofs = ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * FC);
     float acc[FC];
 #pragma unroll
@@ -335,10 +340,13 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
         if (tid == 0) {
             tc::fence_after();
             const uint32_t buf = s_base + (uint32_t)((t & 1) * G::SB);
+            const uint32_t ashift = (t & 1) ? 8u * G::SBO : 0u;   // odd tiles: S rows -> D lanes 64..127
             const int nks = (tile_n(t) + 7) >> 3;
             for (int ks = 0; ks < nks; ++ks) {
-                const uint64_t desc = tc::smem_desc(buf + (uint32_t)(ks * 2 * G::KGB), G::KGB, G::SBO);
-                tc::mma_tf32(dbuf(t), desc, desc, G::IDESC, (ks > 0 || t % FW != 0) ? 1u : 0u);
+                const uint32_t kaddr = buf + (uint32_t)(ks * 2 * G::KGB);
+                const uint64_t adesc = tc::smem_desc(kaddr - ashift, G::KGB, G::SBO);
+                const uint64_t bdesc = tc::smem_desc(kaddr, G::KGB, G::SBO);
+                tc::mma_tf32(dbuf(t), adesc, bdesc, G::IDESC, (ks > 0 || t % FW != 0) ? 1u : 0u);
             }
             tc::mma_commit(&mbar[t & 1]);
         }
@@ -347,7 +355,7 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
             // that ended with it is folded
             ok &= tc::mbar_wait(&mbar[(t - 1) & 1], (uint32_t)(((t - 1) >> 1) & 1));
             tc::fence_after();
-            if (t % FW == 0 && folder) fold(dbuf(t - 1));
+            if (t % FW == 0 && fpar == ((t - 1) & 1)) fold(dbuf(t - 1));
         }
         if (t + 1 < ntiles) product(ents + ((t + 1) % G::SE) * VT, S + ((t + 1) & 1) * G::SB, tile_n(t + 1));
         if (t + 2 < ntiles) load_rows(ents + ((t + 2) % G::SE) * VT, tile_n(t + 2));
@@ -359,14 +367,13 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
     if (ntiles > 0) {
         ok &= tc::mbar_wait(&mbar[(ntiles - 1) & 1], (uint32_t)(((ntiles - 1) >> 1) & 1));
         tc::fence_after();
-        if (folder) fold(dbuf(ntiles - 1));
+        if (fpar == ((ntiles - 1) & 1)) fold(dbuf(ntiles - 1));
     }
     __syncthreads();   // every MMA has finished: S0 becomes the epilogue buffer
-    float* Tb = reinterpret_cast<float*>(S);
-    float* Ts = Tb + RP * G::TSTR;
-    float* bred = Ts + RP * G::TSTR;   // [NT][8]
-    if (folder) {
-        float* T = (warp & 3) == 0 ? Tb : Ts;
+    float* T4 = reinterpret_cast<float*>(S);          // [warp % 4][RP][TSTR]: bb even, sb even, bb odd, sb odd
+    float* bred = T4 + 4 * RP * G::TSTR;              // [NT][8]
+    {
+        float* T = T4 + (warp & 3) * RP * G::TSTR;
 #pragma unroll
         for (int j = 0; j < FC; ++j) T[lane * G::TSTR + (warp >> 2) * FC + j] = acc[j];
     }
@@ -391,7 +398,10 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
             gi = gj;
             gj = t;
         }
-        out[s] = Tb[gi * G::TSTR + gj] + (Ts[gi * G::TSTR + gj] + Ts[gj * G::TSTR + gi]);
+        const int ij = gi * G::TSTR + gj, ji = gj * G::TSTR + gi, L = RP * G::TSTR;
+        const float bb = T4[ij] + T4[2 * L + ij];
+        const float sb = (T4[L + ij] + T4[3 * L + ij]) + (T4[L + ji] + T4[3 * L + ji]);
+        out[s] = bb + sb;
     }
     // b[r]: slot-owner threads th = r/8 (mod SPV), in increasing order
     for (int r = tid; r < RP; r += NT) {
