@@ -403,7 +403,7 @@ def test_oracle_warm_start_begins_cold_and_then_differs(oracle_mod):
     assert not np.array_equal(runs[0][1], runs[1][1])       # second call starts from the kept vector
 
 
-# ---- epoch-permutation sampling variant (SURVEY-ranked next item; Sec. IV epoch) ----
+# ---- epoch-permutation sampling variant (Sec. IV epoch) ----
 
 def test_epoch_permutation_update_matches_dense_masked_formula(oracle_mod):
     """sampler = 1, c = 0.5, AO iteration 3 = slot 1 of epoch 1 (T = 2): M_hat
