@@ -12,9 +12,11 @@
 // visits accumulates D = S big^T in tensor memory: rows 0..R-1 give
 // bb = sum big big^T, rows R..2R-1 give sb = sum small big^T, and
 // G = bb + sb + sb^T (the dropped small small^T is about 2^-24 of G).
-// The tensor core's FP32 accumulation is not round-to-nearest, so D restarts
-// every tile (VT/8 MMAs) and warps 0 and 1 add each finished tile into FP32
-// registers (row i of bb in lane i of warp 0, of sb in lane i of warp 1).
+// The tensor core's FP32 accumulation is biased (measured: accumulating a
+// whole chunk in tensor memory moved G by up to 3e-5 relative), so D restarts
+// every tile (VT/8 MMAs) and a warp pair adds each finished tile into FP32
+// registers: even tiles' rows sit in TMEM lanes 0-63 (bb row i in lane i of
+// warp 0, sb row i in warp 1), odd tiles' in lanes 64-127 (warps 2 and 3).
 // b = sum x_e k_e stays on the FP32 FMA path.
 #pragma once
 
