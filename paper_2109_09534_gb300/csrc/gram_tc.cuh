@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
     using G = GramTC<EW, VT, FW, NTB>;
     using RowT = std::conditional_t<BF16, uint2, float4>;   // 4 factor elements
     constexpr int NT = G::NT, SPV = G::SPV, RS = G::RS, RP = G::RP, ROWB = RP * (BF16 ? 2 : 4), FC = G::FCOLS;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);   // [2]: MMAs of even / odd tiles
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + 16);
     unsigned char* S = smem_raw + G::S_OFF;
