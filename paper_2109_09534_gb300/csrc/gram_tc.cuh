@@ -382,12 +382,12 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
     reinterpret_cast<float4*>(bred)[2 * tid] = make_float4(bq[0], bq[1], bq[2], bq[3]);
     reinterpret_cast<float4*>(bred)[2 * tid + 1] = make_float4(bq[4], bq[5], bq[6], bq[7]);
     tc::fence_before();
-    __syncthreads();
+    const int any_timeout = __syncthreads_or(ok ? 0 : 1);   // a wait that gave up in any thread
     if (warp == 0) {
         tc::fence_after();
         tc::tmem_free(tmem, G::TCOLS);
     }
-    if (!ok && tid == 0 && a.stat_wait) atomicAdd(a.stat_wait, 1ull);
+    if (any_timeout && tid == 0 && a.stat_wait) atomicAdd(a.stat_wait, 1ull);
     // G[i][j] = bb[i][j] + (sb[i][j] + sb[j][i]) from the upper triangle, so
     // that the diagonal tiles are exactly symmetric
     float* out = a.partial + (size_t)item * G::PW;
