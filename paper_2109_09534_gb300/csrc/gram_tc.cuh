@@ -143,7 +143,9 @@ __device__ __forceinline__ float round_tf32(float x) {
 
 // Block shape and shared-memory map of the tensor-core Gram.  FW = tiles per
 // tensor-memory accumulation window (D restarts, and is folded into the
-// registers, every FW tiles).
+// registers, every FW tiles); only 1 is valid with the alternating lane
+// placement below, since an even and an odd tile would add their rows onto
+// each other's ignored rows within one window.
 template <int EW, int VT, int FW, int NT_>
 struct GramTC {
     static constexpr int RP = 32;
@@ -186,7 +188,7 @@ struct GramTC {
     // sums of even and odd tiles [4][RP][RP + 1], then the b partials [NT][8]
     static constexpr int TSTR = RP + 1;
     static_assert(VT % 8 == 0 && VT <= NT && (VT * SPV) % NT == 0 && NT % SPV == 0, "tile shape");
-    static_assert(FW >= 1, "window");
+    static_assert(FW == 1, "one tile per accumulation window (alternating lane placement)");
     static_assert(NT == 128 || NT == 256, "block");
     static_assert(4 * RP * TSTR * 4 + NT * 32 <= 2 * SB, "epilogue fits in S0 and S1");
     static_assert(SBO % 16 == 0 && KGB % 16 == 0, "descriptor offsets are 16-byte multiples");
