@@ -438,3 +438,84 @@ def test_epoch_permutation_update_matches_dense_masked_formula(oracle_mod):
         H = K.T @ np.diag(Mn[p]) @ K + lam * np.eye(R)
         want[p] = np.maximum(0, U[n][p] - grad[p] / np.linalg.eigvalsh(H)[-1])
     np.testing.assert_allclose(o.get_factor(n), want, rtol=1e-11, atol=1e-13)
+
+
+# ---- momentum and extrapolation (Alg. 1 lines 12-13) and the epoch length ----
+
+@pytest.mark.parametrize("c", [1.0, 0.5])
+def test_inner_iterations_match_dense_momentum_replay(oracle_mod, c):
+    """MAX_INNER = 3 on one mode with exact L_p, replayed densely: each inner
+    iteration l rebuilds M_hat_l from the pinned sampler (inner counter l), takes
+    the gradient at the extrapolated point Y_l (lines 6-8 with Y_l, not A_l),
+    A_{l+1} = (Y_l - grad / L_p)_+ (line 11), beta = (sqrt(L_p) - sqrt(lambda)) /
+    (sqrt(L_p) + sqrt(lambda)) (line 12) and Y_{l+1} = A_{l+1} + beta (A_{l+1} -
+    A_l) (line 13).  Rows with k_p = 0 keep A and Y.  Iterations 2 and 3 start
+    from Y_1 and Y_2, so a wrong beta or a wrong extrapolation changes A_3."""
+    rng = np.random.default_rng(21 if c == 1.0 else 22)
+    dims, R, lam = [7, 5, 4], 3, 0.04
+    cells = full_cells(dims)
+    idx = cells[rng.random(len(cells)) < 0.7]
+    vals = rng.random(idx.shape[0]) * 1.5
+    U = [rng.random((d, R)) + 0.05 for d in dims]
+    n, seed, k_ao, inner = 0, 31, 5, 3
+    o = make_oracle(oracle_mod, dims, R, lam, idx, vals, U, lp_exact=1, max_inner=inner, debug=1)
+    o.ao_iter = k_ao
+    o.snmc(n, c, seed)
+    row_ptr, perm = oracle_mod.bucket(idx, n, dims[n])
+    X = np.zeros(dims)
+    X[tuple(idx.T)] = vals
+    Xn = unfold(X, n)
+    K = kr_for_mode(U, n)
+    A, Y = U[n].copy(), U[n].copy()
+    beta_last = np.zeros(dims[n])
+    for l in range(inner):
+        Mh = np.zeros(dims)
+        for p in range(dims[n]):
+            cnt = row_ptr[p + 1] - row_ptr[p]
+            k = oracle_mod.sample_count(c, cnt)
+            for q in oracle_mod.sample_row(seed, n, k_ao, l, row_ptr[p], cnt, k):
+                Mh[tuple(idx[perm[q]])] = 1
+        Mn = unfold(Mh, n)
+        A_new, Y_new = A.copy(), Y.copy()
+        for p in range(dims[n]):
+            if Mn[p].sum() == 0:
+                continue
+            grad = -(Mn[p] * Xn[p]) @ K + (Mn[p] * (Y[p] @ K.T)) @ K + lam * Y[p]
+            H = K.T @ np.diag(Mn[p]) @ K + lam * np.eye(R)
+            L = np.linalg.eigvalsh(H)[-1]
+            a_next = np.maximum(0.0, Y[p] - grad / L)
+            beta = (np.sqrt(L) - np.sqrt(lam)) / (np.sqrt(L) + np.sqrt(lam))
+            A_new[p] = a_next
+            Y_new[p] = a_next + beta * (a_next - A[p])
+            beta_last[p] = beta
+        A, Y = A_new, Y_new
+    np.testing.assert_allclose(o.get_factor(n), A, rtol=1e-11, atol=1e-13)
+    for p in range(dims[n]):
+        d = o.debug_row(p)
+        if d["kp"] > 0:
+            assert d["beta"] == pytest.approx(beta_last[p], rel=1e-11)
+    # the replay is not vacuous: the extrapolated points moved the result
+    assert np.abs(A - U[n]).max() > 1e-3
+
+
+@pytest.mark.parametrize("c,T", [(0.1, 10), (0.3, 4), (0.37, 3), (1.0 / 3.0, 3), (0.25, 4), (1.0, 1)])
+def test_epoch_runs_ceil_one_over_c_ao_iterations(oracle_mod, c, T):
+    """An epoch is the number of AO iterations that touches every observation
+    once on average (Sec. IV): ceil(1/c - 1e-12), so that a 1/c that rounding
+    left just above an integer counts as that integer (c = 1/3 gives 3)."""
+    rng = np.random.default_rng(23)
+    dims, R = [6, 5, 4], 2
+    cells = full_cells(dims)
+    idx = cells[rng.random(len(cells)) < 0.9]
+    vals = rng.random(idx.shape[0])
+    o = make_oracle(oracle_mod, dims, R, 0.01, idx, vals, [rng.random((d, R)) for d in dims])
+    o.ao_iter = 7
+    o.epoch(c, seed=3)
+    assert o.ao_iter == 7 + T
+    # every AO iteration updated every mode: the visits are T times one
+    # iteration's sum over the modes of floor(c n_p)
+    per_iter = 0
+    for m in range(3):
+        counts = np.bincount(idx[:, m], minlength=dims[m])
+        per_iter += int(np.floor(c * counts.astype(np.float64)).sum())
+    assert o.visits == T * per_iter
