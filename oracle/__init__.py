@@ -115,7 +115,8 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def sample_key(seed: int, mode: int, ao_iter: int, inner: int, q: int) -> int:
-    """Sample key of bucket position q (Sec. II-B sampling reading)."""
+    """Sample key of bucket position q (Sec. II-B sampling reading): word
+    q mod 4 of the Philox4x32-10 block with counter {mode, ao_iter, inner, q // 4}."""
     return int(_lib().orc_sample_key(seed, mode, ao_iter, inner, q))
 
 

@@ -41,16 +41,17 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* Sample key of bucket position q: word 0 of Philox4x32-10 with counter
- * {mode, ao_iter, inner, q} and the 64-bit seed as the key (low word first).
- * The paper only says "sample, uniformly at random" (Sec. II-B, Alg. 1
- * line 5); this counter-based key makes the sample reproducible. */
+/* Sample key of bucket position q: word q mod 4 of Philox4x32-10 with
+ * counter {mode, ao_iter, inner, floor(q / 4)} and the 64-bit seed as the key
+ * (low word first), so that one block gives the keys of four consecutive
+ * positions.  The paper only says "sample, uniformly at random" (Sec. II-B,
+ * Alg. 1 line 5); this counter-based key makes the sample reproducible. */
 uint32_t orc_sample_key(uint64_t seed, uint32_t mode, uint64_t ao_iter, uint32_t inner, int64_t q) {
-    uint32_t ctr[4] = {mode, (uint32_t)ao_iter, inner, (uint32_t)q};
+    uint32_t ctr[4] = {mode, (uint32_t)ao_iter, inner, (uint32_t)(q / 4)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t out[4];
     orc_philox4x32_10(ctr, key, out);
-    return out[0];
+    return out[q % 4];
 }
 
 /* B_{l,p} = floor(c ||M(p,:)||_0), Sec. II-B. */

@@ -19,8 +19,9 @@
  * code that applies it):
  *   - sample (Alg. 1 line 5, Sec. II-B): a uniform k_p-subset without
  *     replacement, k_p = floor(c * n_p) in IEEE double; the subset is the k_p
- *     bucket positions with the smallest (key, position), key = word 0 of
- *     Philox4x32-10(counter = {mode, ao_iter, inner, position}, key = seed).
+ *     bucket positions with the smallest (key, position), key = word
+ *     (position mod 4) of Philox4x32-10(counter = {mode, ao_iter, inner,
+ *     floor(position / 4)}, key = seed).
  *   - L_p (Alg. 1 line 10): power method from v0 = 1/sqrt(R) * ones, a fixed
  *     number of iterations, Rayleigh quotient of the last iterate.  An exact
  *     Jacobi eigenvalue solve is kept for reporting and for the step-size pins.

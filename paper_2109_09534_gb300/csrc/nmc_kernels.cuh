@@ -823,8 +823,18 @@ __global__ void __launch_bounds__(kLightThreads, 4) k_light(ModeArgs a) {
     // Alg. 1 line 5: the k smallest (key, position) of the row's n positions
     unsigned long long T = ~0ull;
     if (k < n) {
+        // one Philox block per thread gives the keys of 4 consecutive positions
         const KeyGen kg(a.ss);
-        for (int j = threadIdx.x; j < n; j += LT) keys[j] = kg.key(uq0 + j);
+        const uint32_t g0 = uq0 >> 2, g1 = (uq0 + (uint32_t)n + 3u) >> 2;
+        for (uint32_t g = g0 + threadIdx.x; g < g1; g += LT) {
+            const uint4 w = kg.key4(g);
+            const uint32_t kw[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (uint32_t t = 0; t < 4; ++t) {
+                const uint32_t q = 4u * g + t;
+                if (q >= uq0 && q - uq0 < (uint32_t)n) keys[q - uq0] = kw[t];
+            }
+        }
         __syncthreads();
         auto get = [&](int j) -> unsigned long long {
             return ((unsigned long long)keys[j] << 32) | (unsigned long long)(uq0 + j);
@@ -902,16 +912,19 @@ __global__ void __launch_bounds__(RowFinish<RP>::WARPS * 32) k_rows_finish(ModeA
 // Heavy rows, step 1: per chunk of a row, keys of every position; positions
 // with key < lo are certainly in the sample and are written, in position
 // order; lo <= key < hi are candidates whose fate depends on the whole row.
-// Each thread takes 16 consecutive positions per round, so one block scan
-// serves 4096 positions (measured: 8 per thread 7.6, 16 per thread 7.1 ms per
-// epoch on the Zipf(1.1) 10^4-cube).
+// Each thread takes 16 consecutive positions per round, the keys of four
+// Philox blocks, so one block scan serves 4096 positions (measured with one
+// block per key: 8 positions per thread 7.6, 16 per thread 7.1 ms per epoch on
+// the Zipf(1.1) 10^4-cube).
 constexpr int kSamplePer = 16;   // positions per thread per round of the split-row sampler
 constexpr int kResolvePer = 8;   // candidates per thread per round of the resolver's compaction
 
 // Keys of chunk `ch`: certain positions to a.vis[pb ...] in position order,
 // candidates to the chunk's candidate slots; returns the certain count (the
-// same in every thread).
+// same in every thread).  Rounds start at pb rounded down to a multiple of 4,
+// so that a thread's 16 positions are four whole Philox blocks.
 __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan_tmp) {
+    static_assert(kSamplePer % 4 == 0, "whole Philox blocks per thread");
     const int4 c = a.chunks[ch];
     const int h = c.x;
     const uint32_t pb = (uint32_t)c.y, pe = (uint32_t)c.z;
@@ -923,16 +936,25 @@ __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan
     const uint32_t lo = lo_all ? 0u : (uint32_t)br.x, hi = hi_all ? 0u : (uint32_t)br.y;
     const KeyGen kg(a.ss);
     int nsel = 0, ncand = 0;
-    for (uint32_t base = pb; base < pe; base += kThreads * kSamplePer) {
+    for (uint32_t base = pb & ~3u; base < pe; base += kThreads * kSamplePer) {
         const uint32_t q0 = base + threadIdx.x * kSamplePer;
+        uint32_t kv[kSamplePer];
+#pragma unroll
+        for (int b = 0; b < kSamplePer / 4; ++b) {
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (q0 + 4u * b < pe) w = kg.key4((q0 >> 2) + b);
+            kv[4 * b] = w.x;
+            kv[4 * b + 1] = w.y;
+            kv[4 * b + 2] = w.z;
+            kv[4 * b + 3] = w.w;
+        }
         // bit j of dm / cm: position q0 + j is certain / a candidate
         unsigned dm = 0u, cm = 0u;
 #pragma unroll
         for (int j = 0; j < kSamplePer; ++j) {
-            const uint32_t key = kg.key(q0 + j);
-            const bool in = q0 + j < pe;
-            const bool d = in && (lo_all || key < lo);
-            const bool cn = in && !d && (hi_all || key < hi);
+            const bool in = q0 + j >= pb && q0 + j < pe;
+            const bool d = in && (lo_all || kv[j] < lo);
+            const bool cn = in && !d && (hi_all || kv[j] < hi);
             dm |= (unsigned)d << j;
             cm |= (unsigned)cn << j;
         }
@@ -944,12 +966,14 @@ __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan
             dm &= dm - 1u;
             a.vis[pb + od++] = q0 + j;
         }
-        while (cm) {   // about one position in thirty: the key is recomputed
-            const int j = __ffs(cm) - 1;
-            cm &= cm - 1u;
-            const uint32_t q = q0 + j;
-            if (oc < cap) a.cand[cand_off + oc] = ((unsigned long long)kg.key(q) << 32) | q;
-            ++oc;
+        if (cm) {   // about one position in thirty
+#pragma unroll
+            for (int j = 0; j < kSamplePer; ++j) {
+                if ((cm >> j) & 1u) {
+                    if (oc < cap) a.cand[cand_off + oc] = ((unsigned long long)kv[j] << 32) | (q0 + j);
+                    ++oc;
+                }
+            }
         }
         nsel += tot & 0xFFFF;
         ncand += tot >> 16;

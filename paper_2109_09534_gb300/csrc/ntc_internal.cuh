@@ -23,22 +23,6 @@ struct alignas(EW * 4) Entry {
 
 // ---- Philox4x32-10 (Salmon et al., SC'11): two 32x32 multiplies per round,
 // high halves xored with the other words and the round key; Weyl key bumps.
-__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2,
-                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
-        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
-        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        c1 = (uint32_t)p1;
-        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-        c3 = (uint32_t)p0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c0;
-}
-
 __device__ __forceinline__ uint4 philox4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                          uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -56,18 +40,17 @@ __device__ __forceinline__ uint4 philox4(uint32_t c0, uint32_t c1, uint32_t c2, 
 }
 
 // Sampling stream of one (mode, AO iteration, inner iteration): the key of
-// bucket position q is word 0 of Philox(counter {mode, k, l, q}, key seed).
+// bucket position q is word q mod 4 of Philox(counter {mode, k, l, q / 4},
+// key seed), so one block gives the keys of four consecutive positions.
 struct SampleStream {
     uint32_t mode, iter, inner, k0, k1;
-    __device__ __forceinline__ uint32_t key(uint32_t q) const {
-        return philox_word0(mode, iter, inner, q, k0, k1);
-    }
 };
 
 // Keys of one sampling stream with the uniform part precomputed.  Within a
-// launch only the counter's last word (the bucket position q) varies, so in
-// rounds 1-3 of Philox4x32-10 one product per round depends on q and the
-// other is the same for every key.  key(q) returns exactly SampleStream::key(q).
+// launch only the counter's last word (the block index g = q / 4) varies, so
+// in rounds 1-3 of Philox4x32-10 one product per round depends on g and the
+// other is the same for every block.  key4(g) returns the four words of block
+// g (the keys of positions 4g .. 4g+3), key(q) the key of one position.
 struct KeyGen {
     uint32_t A, B, D, E, F, k0, k1;
     __device__ explicit KeyGen(const SampleStream& s) : k0(s.k0), k1(s.k1) {
@@ -75,7 +58,7 @@ struct KeyGen {
         // round 1 on (mode, iter, inner, .): words 0, 1, 3 are uniform
         const unsigned long long p0 = (unsigned long long)M0 * s.mode, p1 = (unsigned long long)M1 * s.inner;
         const uint32_t c0_1 = (uint32_t)(p1 >> 32) ^ s.iter ^ k0, c1_1 = (uint32_t)p1, c3_1 = (uint32_t)p0;
-        A = (uint32_t)(p0 >> 32) ^ k1;            // word 2 after round 1 is A ^ q
+        A = (uint32_t)(p0 >> 32) ^ k1;            // word 2 after round 1 is A ^ g
         // round 2: the product of word 0 is uniform
         B = c1_1 ^ (k0 + W0);
         const unsigned long long u0 = (unsigned long long)M0 * c0_1;
@@ -86,9 +69,9 @@ struct KeyGen {
         F = (uint32_t)u1;
         E = c3_2 ^ (k1 + 2u * W1);
     }
-    __device__ __forceinline__ uint32_t key(uint32_t q) const {
+    __device__ __forceinline__ uint4 key4(uint32_t g) const {
         constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-        const unsigned long long p1 = (unsigned long long)M1 * (A ^ q);
+        const unsigned long long p1 = (unsigned long long)M1 * (A ^ g);
         const uint32_t c1_2 = (uint32_t)p1;
         const unsigned long long p0 = (unsigned long long)M0 * ((uint32_t)(p1 >> 32) ^ B);
         uint32_t c0 = c1_2 ^ D, c1 = F, c2 = (uint32_t)(p0 >> 32) ^ E, c3 = (uint32_t)p0;
@@ -104,7 +87,12 @@ struct KeyGen {
             r0 += W0;
             r1 += W1;
         }
-        return c0;
+        return make_uint4(c0, c1, c2, c3);
+    }
+    __device__ __forceinline__ uint32_t key(uint32_t q) const {
+        const uint4 w = key4(q >> 2);
+        const uint32_t j = q & 3u;
+        return j == 0u ? w.x : j == 1u ? w.y : j == 2u ? w.z : w.w;
     }
 };
 
@@ -292,7 +280,8 @@ struct ModeArgs {
     const int32_t* vis_off;
     int n_light;
     unsigned long long* stat_fallback;  // counter of rows that used the exact selector
-    unsigned long long* stat_wait;      // counter of tensor-core waits that timed out
+    unsigned long long* stat_wait;      // tensor-core blocks whose wait timed out: [0] this call, [1] since creation
+    long long test_stall_cycles;        // test hook: > 0 makes block 0 of a tensor-core Gram time out
     uint8_t* mask_out;        // sampler-only mode: mask over bucket positions
 };
 

@@ -30,11 +30,25 @@ def test_philox_known_answers(oracle_mod):
         assert [int(v) for v in got] == out
 
 
-def test_sample_key_is_word0_of_counter(oracle_mod):
+def test_sample_key_is_word_q_mod_4_of_block_q_div_4(oracle_mod):
     seed = 0x0123456789ABCDEF
-    for mode, k, l, q in [(0, 0, 0, 0), (2, 7, 1, 12345), (3, 2**31 + 5, 4, 2**31 - 1)]:
-        w = oracle_mod.philox4x32_10([mode, k & 0xFFFFFFFF, l, q], [seed & 0xFFFFFFFF, seed >> 32])
-        assert oracle_mod.sample_key(seed, mode, k, l, q) == int(w[0])
+    for mode, k, l, q in [(0, 0, 0, 0), (0, 0, 0, 3), (2, 7, 1, 12345), (2, 7, 1, 12346),
+                          (3, 2**31 + 5, 4, 2**31 - 1), (1, 9, 0, 2**31 - 4)]:
+        w = oracle_mod.philox4x32_10([mode, k & 0xFFFFFFFF, l, q // 4], [seed & 0xFFFFFFFF, seed >> 32])
+        assert oracle_mod.sample_key(seed, mode, k, l, q) == int(w[q % 4])
+
+
+def test_keys_of_one_block_are_jointly_uniform(oracle_mod):
+    """The four positions that share a Philox block: the joint histogram of the
+    top 3 bits of the keys of positions 4g + j and 4g + j + 1 over 8192 blocks
+    is flat (chi2, 63 dof), for each neighbouring pair of words."""
+    for j in range(3):
+        a = np.array([oracle_mod.sample_key(11, 2, 5, 0, 4 * g + j) for g in range(8192)], dtype=np.uint64)
+        b = np.array([oracle_mod.sample_key(11, 2, 5, 0, 4 * g + j + 1) for g in range(8192)], dtype=np.uint64)
+        cell = ((a >> 29) * 8 + (b >> 29)).astype(np.int64)
+        h = np.bincount(cell, minlength=64)
+        chi2 = ((h - 128.0) ** 2 / 128.0).sum()
+        assert chi2 < 110.0  # p ~ 2e-4 at 63 dof
 
 
 def test_philox_uniformity(oracle_mod):
