@@ -101,7 +101,10 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
  * Must be called before ntc_set_observed for "keep_perm".  Errors: NTC_ERR_ARG. */
 ntc_status ntc_set_param(ntc_handle* h, const char* key, double value);
 /* (also "profile": 1 brackets every mode-update kernel with CUDA events, see
- * ntc_get_profile) */
+ * ntc_get_profile; and the test hook "test_gram_stall": N > 0 makes block 0
+ * of every tensor-core Gram launch wait up to N SM cycles on a phase that no
+ * MMA was committed to, before it issues any, so that its bounded wait gives
+ * up with nothing in flight -- default 0, off) */
 
 /* Enqueue all further work on this cudaStream_t (e.g. a PyTorch stream);
  * NULL selects the legacy default stream.  Errors: none besides NTC_ERR_ARG. */
@@ -122,9 +125,10 @@ ntc_status ntc_set_observed_dev(ntc_handle* h, int64_t nnz, const int32_t* idx_d
  * observation once on average, Sec. IV); in each, every mode in mode_order
  * (a permutation of 0..order-1; NULL means 0..order-1) is updated by
  * Algorithm 1 with minibatch fraction c (Sec. II-B: row p draws
- * floor(c n_p) of its n_p observations uniformly without replacement).  The
- * sample of bucket position q is fixed by Philox4x32-10 with counter
- * {mode, AO iteration, inner iteration, q} and key `seed`.  Modes updated
+ * floor(c n_p) of its n_p observations uniformly without replacement): the
+ * k_p positions of the row with the smallest (key, position), where the key
+ * of bucket position q is word q mod 4 of Philox4x32-10 with counter
+ * {mode, AO iteration, inner iteration, q / 4} and key `seed`.  Modes updated
  * earlier in the AO iteration are used by later ones (Gauss-Seidel, Sec. III).
  * Enqueued on the stream; returns without synchronising.  0 < c <= 1.
  * Errors: NTC_ERR_STATE before ntc_set_observed, NTC_ERR_ARG. */
@@ -137,7 +141,8 @@ ntc_status ntc_snmc(ntc_handle* h, int mode, double c, uint64_t seed);
 /* CPD model (eq. 1) at n host indices idx[n][order]; out[n] float32 (host).
  * Errors: NTC_ERR_INDEX, NTC_ERR_ARG. */
 ntc_status ntc_predict(ntc_handle* h, int64_t n, const int32_t* idx, float* out);
-/* Same with device buffers; enqueued, not synchronised; indices not checked. */
+/* Same with device buffers; enqueued, not synchronised.  The indices are
+ * checked on the device: a query with an index out of range gives NaN. */
 ntc_status ntc_predict_dev(ntc_handle* h, int64_t n, const int32_t* idx_dev, float* out_dev);
 
 /* Root mean squared error of the model against vals[n] at idx[n][order]
@@ -157,7 +162,8 @@ ntc_status ntc_set_factor(ntc_handle* h, int mode, const float* in);
 ntc_status ntc_get_state(ntc_handle* h, uint64_t* ao_iter);
 ntc_status ntc_set_state(ntc_handle* h, uint64_t ao_iter);
 
-/* Wait for all work enqueued by this handle. */
+/* Wait for all work enqueued by this handle.  NTC_ERR_CUDA if a kernel failed
+ * or a tensor-core Gram wait gave up (see ntc_stats). */
 ntc_status ntc_sync(ntc_handle* h);
 
 /* Counters of the last ntc_epoch/ntc_snmc: visits = sum over row updates of
@@ -166,8 +172,11 @@ ntc_status ntc_sync(ntc_handle* h);
  * the exact fallback selector, the algorithmic bytes moved (index, value and
  * factor-row reads per visit, factor-row reads/writes per row update), the
  * number of kernel launches enqueued, and the number of tensor-core Gram blocks
- * whose bounded wait for their MMAs gave up (0 unless the device misbehaved;
- * their partial sums are then not valid). */
+ * whose bounded wait (about one second) for their MMAs gave up (0 unless the
+ * device misbehaved).  Such a block stops, frees its tensor memory and writes
+ * no partial sums, so the rows it served are not valid: the next call that
+ * synchronises the stream (ntc_sync, ntc_get_factor, ntc_predict, ntc_rmse,
+ * ntc_cost) returns NTC_ERR_CUDA with a message, once per new timeout. */
 typedef struct {
     int64_t visits;
     int64_t visits_heavy;
@@ -217,16 +226,20 @@ ntc_status ntc_sample_mask(ntc_handle* h, int mode, double c, uint64_t seed, uin
  * whose caching allocator owns the device memory and must not see the
  * device-wide synchronisation that cudaMalloc/cudaFree can bring.  Same result
  * as ntc_rmse, but idx_dev[n][order] (int32) and vals_dev[n] (float32) are
- * DEVICE pointers on the handle's device, which must be current; the indices
- * are not checked.  *out (host) receives the RMSE; the call synchronises the
- * handle's stream.  It calls no cudaMalloc/cudaFree: its scratch is a fixed
- * 32 KB array in the library's device memory, one double per block of 2048
- * queries, so n may be at most 4096 * 2048 = 8,388,608 (larger n returns
- * NTC_ERR_ARG).  The first call on a device looks up that array's address,
- * so make that first call before any stream capture.  All calls share the
- * array: calls that overlap on the GPU (other streams, other threads, other
- * handles on the same device) race and must be serialised by the caller.
- * Errors: NTC_ERR_ARG, NTC_ERR_STATE (handle's device not current), NTC_ERR_CUDA. */
+ * DEVICE pointers on the handle's device, which must be current.  The indices
+ * are checked on the device: if any is out of range the call returns
+ * NTC_ERR_INDEX (no factor row is read for that query).  *out (host) receives
+ * the RMSE; the call synchronises the handle's stream.  It calls no
+ * cudaMalloc/cudaFree: its scratch is a fixed 32 KB array in the library's
+ * device memory, one double per block of 2048 queries, so n may be at most
+ * 4096 * 2048 = 8,388,608 (larger n returns NTC_ERR_ARG).  The first call on a
+ * device looks up that array's address (a failed lookup is tried again on the
+ * next call), so make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams, other
+ * threads, other handles on the same device) race and must be serialised by
+ * the caller.
+ * Errors: NTC_ERR_ARG, NTC_ERR_INDEX, NTC_ERR_STATE (handle's device not
+ * current), NTC_ERR_CUDA. */
 ntc_status ntc_rmse_noalloc(ntc_handle* h, int64_t n, const int32_t* idx_dev, const float* vals_dev, double* out);
 
 /* Message for the last failed call on h ("" if none); valid until the next call. */

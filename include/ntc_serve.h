@@ -93,6 +93,10 @@ ntc_status ntc_server_create(double hbm_budget, int max_running, ntc_server** ou
 /* "max_enqueue_per_step": at most this many epochs are enqueued by one tick
  * (default unlimited), the scan resuming where the previous tick stopped, so
  * that a tick stays short and queries issued between ticks are served soon.
+ * "test_gram_stall": test hook, the handle parameter of that name for jobs
+ * submitted from now on (default 0, off).
+ * A job whose epoch reports a tensor-core Gram block that gave up a bounded
+ * wait (ntc_stats.wait_timeouts) ends in NTC_JOB_FAILED.
  * NTC_ERR_ARG for an unknown key or a value out of range. */
 ntc_status ntc_server_set_param(ntc_server* s, const char* key, double value);
 

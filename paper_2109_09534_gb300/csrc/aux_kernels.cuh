@@ -425,8 +425,17 @@ __global__ void k_to_bf16(const float* U, uint16_t* Ub, int64_t n) {
 struct FactorSet {
     const float* U[kMaxOrder];
     const int32_t* inv[kMaxOrder];   // original row -> storage row
+    int64_t dims[kMaxOrder];
     int order, R, rp;
 };
+
+// Every index of the tuple in [0, dims[i]): the kernels that take indices
+// from device memory the host has not validated test this before any read.
+__device__ __forceinline__ bool index_ok(const FactorSet& f, const int32_t* ix) {
+    bool ok = true;
+    for (int i = 0; i < f.order; ++i) ok = ok && ix[i] >= 0 && (int64_t)ix[i] < f.dims[i];
+    return ok;
+}
 
 // Model value (eq. 1) at one index, float32 products and sum.
 __device__ __forceinline__ float model_at(const FactorSet& f, const int32_t* ix) {
@@ -441,28 +450,44 @@ __device__ __forceinline__ float model_at(const FactorSet& f, const int32_t* ix)
     return acc;
 }
 
+// Model values at n index tuples; a tuple with an index out of range gives NaN
+// and reads no factor.
 __global__ void k_predict(FactorSet f, const int32_t* idx, int64_t n, float* out) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = model_at(f, idx + e * f.order);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t* ix = idx + e * f.order;
+        out[e] = index_ok(f, ix) ? model_at(f, ix) : __int_as_float(0x7fc00000);
+    }
 }
 
 // Queries of several jobs in one launch: query e reads job table[slot[e]] at
 // the index idx[e * kMaxOrder ...] (entries past that job's order unused).
 __global__ void k_predict_multi(const FactorSet* table, const int32_t* slot, const int32_t* idx, int64_t n,
                                 float* out) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = model_at(table[slot[e]], idx + e * kMaxOrder);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const FactorSet& f = table[slot[e]];
+        const int32_t* ix = idx + e * kMaxOrder;
+        out[e] = index_ok(f, ix) ? model_at(f, ix) : __int_as_float(0x7fc00000);
+    }
 }
 
-// Per-block double sums of (x - model)^2.
+// Per-block double sums of (x - model)^2.  A tuple with an index out of range
+// is left out of the sum and, if `bad` is not null, sets *bad to 1.
 __global__ void __launch_bounds__(kThreads) k_sq_resid(FactorSet f, const int32_t* idx, const float* vals,
-                                                       int64_t n, double* partial) {
+                                                       int64_t n, double* partial,
+                                                       unsigned long long* bad = nullptr) {
     __shared__ double sh[kThreads / 32];
     double s = 0.0;
+    bool any_bad = false;
     for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
-        const double d = (double)vals[e] - (double)model_at(f, idx + e * f.order);
+        const int32_t* ix = idx + e * f.order;
+        if (!index_ok(f, ix)) {
+            any_bad = true;
+            continue;
+        }
+        const double d = (double)vals[e] - (double)model_at(f, ix);
         s += d * d;
     }
+    if (any_bad && bad) atomicOr(bad, 1ull);
     const double t = block_sum_d(s, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }

@@ -26,7 +26,9 @@ namespace ntc {
 namespace tc {
 
 // An mbarrier wait gives up after this many SM clock cycles (about one second
-// at 2 GHz); the block records the timeout in the handle's counters.
+// at 2 GHz); the block then stops issuing work, waits (again bounded) for the
+// MMAs it has committed, frees its tensor memory, writes no partial and
+// records the timeout in the handle's counters, which the host reports.
 constexpr long long kWaitCycles = 2000000000ll;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -47,11 +49,12 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the completion of the phase with parity `parity`.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the completion of the phase with parity `parity`: false
+// once `limit` SM clock cycles have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 // Generic-proxy shared-memory stores -> visible to the tensor core's reads.
@@ -326,6 +329,12 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
     const uint32_t tmem = *tslot;
     // D buffer of tile t: windows of FW tiles alternate between the two
     auto dbuf = [&](int t) -> uint32_t { return tmem + (uint32_t)(((t / FW) & 1) * G::N); };
+    bool ok = true;
+    if (a.test_stall_cycles > 0 && blockIdx.x == 0) {
+        // test hook: block 0 waits on a phase that no MMA was committed to, so
+        // that the wait runs out with nothing in flight
+        ok = tc::mbar_wait(&mbar[0], 0u, a.test_stall_cycles);
+    }
     if (ntiles > 0) {
         load_rows(ents, tile_n(0));
         product(ents, S, tile_n(0));
@@ -334,13 +343,14 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
     issue_entries(3, p3);
     cp_async_commit();
     uint32_t pos_next = pos_of(4);
-    bool ok = true;
     const uint32_t s_base = tc::smem_addr(S);
+    int issued = 0;   // tiles whose MMAs were committed
     for (int t = 0; t < ntiles; ++t) {
         cp_async_wait<1>();      // entries of t+2
         tc::fence_async_smem();  // this thread's S stores of tile t
         tc::fence_before();      // and its reads of the D buffer tile t may overwrite
-        __syncthreads();
+        if (__syncthreads_or(ok ? 0 : 1)) break;   // a wait gave up: issue nothing more
+        issued = t + 1;
         if (tid == 0) {
             tc::fence_after();
             const uint32_t buf = s_base + (uint32_t)((t & 1) * G::SB);
@@ -368,10 +378,12 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
         cp_async_commit();
     }
     cp_async_wait<0>();
-    if (ntiles > 0) {
-        ok &= tc::mbar_wait(&mbar[(ntiles - 1) & 1], (uint32_t)(((ntiles - 1) >> 1) & 1));
+    if (issued > 0) {
+        // the last commit covers every MMA this block issued
+        const bool last = tc::mbar_wait(&mbar[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1));
         tc::fence_after();
-        if (fpar == ((ntiles - 1) & 1)) fold(dbuf(ntiles - 1));
+        if (ok && last && issued == ntiles && fpar == ((ntiles - 1) & 1)) fold(dbuf(ntiles - 1));
+        ok &= last;
     }
     __syncthreads();   // every MMA has finished: S0 becomes the epilogue buffer
     float* T4 = reinterpret_cast<float*>(S);          // [warp % 4][RP][TSTR]: bb even, sb even, bb odd, sb odd
@@ -389,7 +401,15 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
         tc::fence_after();
         tc::tmem_free(tmem, G::TCOLS);
     }
-    if (any_timeout && tid == 0 && a.stat_wait) atomicAdd(a.stat_wait, 1ull);
+    if (any_timeout) {
+        // the partial is not valid: leave it unwritten and count the block
+        // (per call and since the handle was created; the host reports it)
+        if (tid == 0 && a.stat_wait) {
+            atomicAdd(a.stat_wait, 1ull);
+            atomicAdd(a.stat_wait + 1, 1ull);
+        }
+        return;
+    }
     // G[i][j] = bb[i][j] + (sb[i][j] + sb[j][i]) from the upper triangle, so
     // that the diagonal tiles are exactly symmetric
     float* out = a.partial + (size_t)item * G::PW;

@@ -257,6 +257,7 @@ ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t a
     a.n_light = p.n_light;
     a.stat_fallback = h->stat.as<unsigned long long>();
     a.stat_wait = h->stat.as<unsigned long long>() + 1;
+    a.test_stall_cycles = h->test_stall_cycles;
     a.mask_out = nullptr;
     return a;
 }
@@ -321,10 +322,37 @@ ntc_status check_ready(ntc_handle* h) {
     return NTC_OK;
 }
 
+// Device counters: [0] rows that used the exact fallback selector and [1]
+// tensor-core Gram blocks whose bounded wait gave up, both for the current
+// call; [2] the latter since the handle was created (never cleared).
 ntc_status reset_stats(ntc_handle* h) {
     h->stats = ntc_stats{};
-    NTC_CUDA(h, h->stat.ensure(2 * sizeof(unsigned long long)));
+    if (!h->stat.p) {
+        NTC_CUDA(h, h->stat.ensure(3 * sizeof(unsigned long long)));
+        NTC_CUDA(h, cudaMemsetAsync(h->stat.p, 0, 3 * sizeof(unsigned long long), h->stream));
+        return NTC_OK;
+    }
     NTC_CUDA(h, cudaMemsetAsync(h->stat.p, 0, 2 * sizeof(unsigned long long), h->stream));
+    return NTC_OK;
+}
+
+// After the handle's stream has been synchronised: a tensor-core Gram block
+// that gave up waiting since the last check left a partial unwritten, so the
+// updates enqueued since then are not valid.  Reported once per new timeout.
+ntc_status check_faults(ntc_handle* h) {
+    if (!h->stat.p) return NTC_OK;
+    unsigned long long total = 0;
+    NTC_CUDA(h, cudaMemcpyAsync(&total, h->stat.as<unsigned long long>() + 2, sizeof(total),
+                                cudaMemcpyDeviceToHost, h->stream));
+    NTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (total > h->faults_seen) {
+        const unsigned long long fresh = total - h->faults_seen;
+        h->faults_seen = total;
+        return fail(h, NTC_ERR_CUDA,
+                    "tensor-core Gram: " + std::to_string(fresh) +
+                        " block(s) gave up a bounded wait for their MMAs; the factors updated since the last "
+                        "successful check are not valid");
+    }
     return NTC_OK;
 }
 
@@ -421,7 +449,7 @@ ntc_status download_factor(ntc_handle* h, int mode, float* out) {
     NTC_CUDA(h, cudaStreamSynchronize(h->stream));
     const std::vector<int32_t>& inv = h->inv_h[mode];
     for (int64_t r = 0; r < I; ++r) memcpy(out + r * R, tmp.data() + (size_t)inv[(size_t)r] * RP, sizeof(float) * R);
-    return NTC_OK;
+    return check_faults(h);
 }
 
 // Store `in` ([dims][rank], original row order, host) as factor `mode`.
@@ -604,6 +632,7 @@ FactorSet factor_set(ntc_handle* h) {
         f.U[i] = h->U[i].as<float>();
         f.inv[i] = h->inv_dev[i].as<int32_t>();
     }
+    for (int i = 0; i < kMaxOrder; ++i) f.dims[i] = i < h->order ? h->dims[i] : 0;
     f.order = h->order;
     f.R = h->rank;
     f.rp = h->rp;
@@ -673,6 +702,15 @@ ntc_status prepare_epoch(ntc_handle* h, double c) {
     return reset_stats(h);
 }
 
+cudaError_t fault_count_enqueue(ntc_handle* h, unsigned long long* host) {
+    if (!h->stat.p) {
+        *host = 0;
+        return cudaSuccess;
+    }
+    return cudaMemcpyAsync(host, h->stat.as<unsigned long long>() + 2, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, h->stream);
+}
+
 int64_t handle_device_bytes(const ntc_handle* h) {
     int64_t b = 0;
     for (int i = 0; i < kMaxOrder; ++i) {
@@ -697,30 +735,34 @@ int64_t handle_device_bytes(const ntc_handle* h) {
 }  // namespace ntc
 
 // ---- allocation-free RMSE -----------------------------------------------------
-// One double of partial sum per block of kNoAllocPerBlock queries, plus the
-// final sum, in a file-scope device array: every GPU that loads the library
-// holds these 32 KB until the process exits, and every call shares them.
+// One double of partial sum per block of kNoAllocPerBlock queries, then the
+// final sum and the out-of-range flag, in a file-scope device array: every GPU
+// that loads the library holds these 32 KB until the process exits, and every
+// call shares them.
 constexpr int kNoAllocPerBlock = 2048;
 constexpr int kNoAllocMaxBlocks = 4096;
 constexpr int64_t kNoAllocMaxQueries = (int64_t)kNoAllocPerBlock * kNoAllocMaxBlocks;
-static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 1];
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 2];
 
 namespace {
 constexpr int kNoAllocMaxDevices = 64;
-std::once_flag g_noalloc_once[kNoAllocMaxDevices];
-cudaError_t g_noalloc_err[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[kNoAllocMaxDevices];
 
-// Device address of the scratch array for the current device, looked up once
-// per device.  The array's name in host code is only a host-side stand-in.
+// Device address of the scratch array on the current device `dev` (the
+// array's name in host code is only a host-side stand-in).  Only a successful
+// lookup is kept, so a call after a failed one (e.g. one made during stream
+// capture) looks it up again.
 cudaError_t noalloc_scratch(int dev, double** out) {
-    std::call_once(g_noalloc_once[dev], [dev] {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
         void* p = nullptr;
-        g_noalloc_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = static_cast<double*>(p);
-    });
+    }
     *out = g_noalloc_ptr[dev];
-    return g_noalloc_err[dev];
+    return cudaSuccess;
 }
 }  // namespace
 
@@ -815,6 +857,9 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
         h->sampler = (int)v;
     } else if (k == "gram_tc") {
         h->gram_tc = v != 0.0 ? 1 : 0;
+    } else if (k == "test_gram_stall") {
+        if (!(v >= 0 && v <= 1e9)) return fail(h, NTC_ERR_ARG, "test_gram_stall must be in [0, 1e9] cycles");
+        h->test_stall_cycles = (long long)v;
     } else if (k == "cache_staging") {
         h->cache_staging = v != 0.0 ? 1 : 0;
     } else if (k == "bracket_z") {
@@ -915,7 +960,7 @@ ntc_status ntc_predict(ntc_handle* h, int64_t n, const int32_t* idx, float* out)
     NTC_CUDA(h, cudaGetLastError());
     NTC_CUDA(h, cudaMemcpyAsync(out, dout.p, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
     NTC_CUDA(h, cudaStreamSynchronize(h->stream));
-    return NTC_OK;
+    return check_faults(h);
 }
 
 ntc_status ntc_rmse(ntc_handle* h, int64_t n, const int32_t* idx, const float* vals, double* out) {
@@ -941,7 +986,7 @@ ntc_status ntc_rmse(ntc_handle* h, int64_t n, const int32_t* idx, const float* v
     NTC_CUDA(h, cudaMemcpyAsync(&s, tot.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     NTC_CUDA(h, cudaStreamSynchronize(h->stream));
     *out = std::sqrt(s / (double)n);
-    return NTC_OK;
+    return check_faults(h);
 }
 
 ntc_status ntc_cost(ntc_handle* h, double* out) {
@@ -970,7 +1015,7 @@ ntc_status ntc_cost(ntc_handle* h, double* out) {
     fit = t[0];
     for (int i = 0; i < h->order; ++i) reg += t[1 + i];
     *out = 0.5 * fit + 0.5 * h->lambda * reg;
-    return NTC_OK;
+    return check_faults(h);
 }
 
 ntc_status ntc_get_factor(ntc_handle* h, int mode, float* out) {
@@ -1005,8 +1050,9 @@ ntc_status ntc_set_state(ntc_handle* h, uint64_t ao_iter) {
 
 ntc_status ntc_sync(ntc_handle* h) {
     if (!h) return NTC_ERR_ARG;
+    h->err.clear();
     NTC_CUDA(h, cudaStreamSynchronize(h->stream));
-    return NTC_OK;
+    return check_faults(h);
 }
 
 ntc_status ntc_get_stats(ntc_handle* h, ntc_stats* out) {
@@ -1103,15 +1149,20 @@ ntc_status ntc_rmse_noalloc(ntc_handle* h, int64_t n, const int32_t* idx_dev, co
     double* scratch = nullptr;
     NTC_CUDA(h, noalloc_scratch(dev, &scratch));
     const int nb = (int)((n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
-    // every partial slot 0..nb-1 is written before it is read, and the final
-    // slot is written by the second kernel, so nothing needs clearing
-    k_sq_resid<<<nb, kThreads, 0, h->stream>>>(factor_set(h), idx_dev, vals_dev, n, scratch);
+    // every partial slot 0..nb-1 is written before it is read and the sum
+    // slot by the second kernel; only the out-of-range flag starts at zero
+    unsigned long long* bad = reinterpret_cast<unsigned long long*>(scratch + kNoAllocMaxBlocks + 1);
+    NTC_CUDA(h, cudaMemsetAsync(bad, 0, sizeof(unsigned long long), h->stream));
+    k_sq_resid<<<nb, kThreads, 0, h->stream>>>(factor_set(h), idx_dev, vals_dev, n, scratch, bad);
     k_sum_partials<<<1, kThreads, 0, h->stream>>>(scratch, nb, scratch + kNoAllocMaxBlocks);
     NTC_CUDA(h, cudaGetLastError());
-    double s = 0.0;
-    NTC_CUDA(h, cudaMemcpyAsync(&s, scratch + kNoAllocMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    double res[2] = {0.0, 0.0};   // the sum, then the flag's bits
+    NTC_CUDA(h, cudaMemcpyAsync(res, scratch + kNoAllocMaxBlocks, sizeof(res), cudaMemcpyDeviceToHost, h->stream));
     NTC_CUDA(h, cudaStreamSynchronize(h->stream));
-    *out = std::sqrt(s / (double)n);
+    unsigned long long flag = 0;
+    memcpy(&flag, &res[1], sizeof(flag));
+    if (flag != 0) return fail(h, NTC_ERR_INDEX, "ntc_rmse_noalloc: a query index is out of range");
+    *out = std::sqrt(res[0] / (double)n);
     return NTC_OK;
 }
 

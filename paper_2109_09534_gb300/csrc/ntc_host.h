@@ -102,6 +102,10 @@ struct ntc_handle {
     ntc::DevMem partial, partial2, row_sum, stat, red, mask;
     int pipeline = 1;
     int gram_tc = 1;         // split-row Gram on the tensor cores where a kernel exists (R_pad 32, orders 2-4)
+    // tensor-core Gram blocks that gave up a bounded wait, as last reported
+    // to the caller; test hook that makes block 0 of each such launch give up
+    unsigned long long faults_seen = 0;
+    long long test_stall_cycles = 0;
     uint64_t upd = 0;                       // mode updates launched so far
     cudaStream_t samp = nullptr;            // split-row sampling stream
     cudaEvent_t ev_sampled[2] = {}, ev_free[2] = {};
@@ -210,5 +214,9 @@ int64_t handle_device_bytes(const ntc_handle* h);
 // Builds every mode's plan for minibatch fraction c and sizes the epoch
 // scratch, so that the first ntc_epoch at c allocates nothing.
 ntc_status prepare_epoch(ntc_handle* h, double c);
+// Enqueues on the handle's stream a copy of the number of tensor-core Gram
+// blocks that have given up a bounded wait since the handle was created into
+// *host (pinned host memory); 0 if the handle has not run an update.
+cudaError_t fault_count_enqueue(ntc_handle* h, unsigned long long* host);
 
 }  // namespace ntc

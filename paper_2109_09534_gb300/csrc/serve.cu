@@ -39,6 +39,8 @@ struct Job {
     DevMem tidx, tval, scratch;
     DevMem snap[2];                  // factors after epoch e in snap[e % 2]
     double* host_sum = nullptr;      // pinned: squared residual sum of the last RMSE
+    unsigned long long* host_faults = nullptr;   // pinned: tensor-core Gram waits that gave up
+    long long test_stall = 0;        // test hook passed to the job's handle ("test_gram_stall")
     std::vector<float> factors[ntc::kMaxOrder];   // host copy once done
     // admission on a worker thread: 0 idle, 1 running, 2 succeeded, 3 failed
     bool admitting = false;
@@ -116,6 +118,7 @@ struct ntc_server {
     DevMem q_slot, q_idx, q_out, q_table;
     int device = 0;
     int max_enqueue = 1 << 30;        // epochs enqueued per tick
+    long long test_stall = 0;         // "test_gram_stall" for jobs submitted from now on
     size_t rr = 0;                    // round-robin start of the enqueue scan
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -144,6 +147,8 @@ void free_device(Job& j) {
     j.snap[1].release();
     if (j.host_sum) cudaFreeHost(j.host_sum);
     j.host_sum = nullptr;
+    if (j.host_faults) cudaFreeHost(j.host_faults);
+    j.host_faults = nullptr;
     if (j.done_ev) cudaEventDestroy(j.done_ev);
     j.done_ev = nullptr;
     if (j.stream) cudaStreamDestroy(j.stream);
@@ -214,7 +219,9 @@ ntc_status admit_job(Job& j, int device) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&j.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j.done_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&j.host_sum, sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&j.host_faults, sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_err(e, "job stream");
+    *j.host_faults = 0;
     ntc_status r = ntc_create(d.order, d.dims, d.rank, d.lambda, &j.h);
     if (r != NTC_OK) return j.admit_err = "ntc_create failed", r;
     auto chk = [&](ntc_status q) -> bool {
@@ -226,6 +233,7 @@ ntc_status admit_job(Job& j, int device) {
     if (!chk(ntc_set_stream(j.h, j.stream)) || !chk(ntc_set_param(j.h, "storage_bf16", d.storage_bf16 ? 1.0 : 0.0)) ||
         !chk(ntc_set_param(j.h, "init_seed", (double)d.init_seed)) ||
         !chk(ntc_set_param(j.h, "cache_staging", 0.0)) ||
+        !chk(ntc_set_param(j.h, "test_gram_stall", (double)j.test_stall)) ||
         !chk(ntc_set_observed(j.h, d.nnz, d.idx, d.vals)) || !chk(ntc::prepare_epoch(j.h, d.c)))
         return r;
     for (int64_t q = 0; q < d.n_test * d.order; ++q) {
@@ -262,6 +270,7 @@ ntc_status enqueue_epoch(ntc_server* s, Job& j) {
     if (e == cudaSuccess)
         e = ntc::rmse_enqueue(j.h, j.tidx.as<int32_t>(), j.tval.as<float>(), j.d.n_test, j.scratch.as<double>(),
                               j.host_sum);
+    if (e == cudaSuccess) e = ntc::fault_count_enqueue(j.h, j.host_faults);
     if (e == cudaSuccess) e = cudaEventRecord(j.done_ev, j.stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "epoch enqueue");
     j.busy = true;
@@ -309,6 +318,11 @@ ntc_status ntc_server_set_param(ntc_server* s, const char* key, double value) {
         s->max_enqueue = (int)value;
         return NTC_OK;
     }
+    if (k == "test_gram_stall") {   // test hook for jobs submitted from now on
+        if (!(value >= 0.0 && value <= 1e9)) return s->fail(NTC_ERR_ARG, "test_gram_stall must be in [0, 1e9]");
+        s->test_stall = (long long)value;
+        return NTC_OK;
+    }
     return s->fail(NTC_ERR_ARG, "unknown server parameter: " + k);
 }
 
@@ -326,6 +340,7 @@ ntc_status ntc_server_submit(ntc_server* s, const ntc_job_desc* desc, int64_t* j
     j->info.t_arrival = desc->arrival;
     j->info.t_admit = j->info.t_done = -1.0;
     j->info.bytes = bytes;
+    j->test_stall = s->test_stall;
     // arrival order, ties by id
     auto pos = std::upper_bound(s->queue.begin(), s->queue.end(), desc->arrival,
                                 [&](double t, int64_t id) { return t < s->jobs[(size_t)id]->d.arrival; });
@@ -368,6 +383,11 @@ ntc_status ntc_server_step(ntc_server* s, int64_t* running, int64_t* queued) {
             return NTC_ERR_CUDA;
         }
         j.busy = false;
+        if (*j.host_faults > 0) {   // a bounded wait gave up: this epoch's factors are not valid
+            fail_job(s, j, "tensor-core Gram: " + std::to_string(*j.host_faults) +
+                               " block(s) gave up a bounded wait; the job's factors are not valid");
+            continue;
+        }
         j.info.epochs += 1;
         j.info.rmse = std::sqrt(*j.host_sum / (double)j.d.n_test);
         s->st.epochs += 1;

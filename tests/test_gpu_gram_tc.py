@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_2109_09534_gb300 import synth
 
-from gpu_helpers import pair, rel_err, require_gpu, small_zipf
+from gpu_helpers import assert_factor_close, pair, rel_err, require_gpu, small_zipf
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,7 @@ def test_single_update_tensor_gram(torch, case, split):
     got, st = one_update(p, torch, 1, split)
     assert st["visits_heavy"] > 0 and st["wait_timeouts"] == 0
     for m, (a, want) in enumerate(got):
-        assert rel_err(a, want) <= 1e-6, (case, split, m, rel_err(a, want))
+        assert_factor_close(a, want, 1e-6, 1e-5, str((case, split, m, rel_err(a, want))))
 
 
 @pytest.mark.parametrize("case", ["zipf2k_r32", "order4_r32"])
@@ -63,7 +63,7 @@ def test_tensor_gram_matches_fma_gram(torch, case):
     tc, _ = one_update(p, torch, 1, "small")
     fma, _ = one_update(p, torch, 0, "small")
     for m in range(p.order):
-        assert rel_err(tc[m][0], fma[m][0]) <= 1e-6, m
+        assert_factor_close(tc[m][0], fma[m][0], 1e-6, 1e-5, str(m))
 
 
 def test_tensor_gram_bf16_storage(torch):
@@ -73,7 +73,7 @@ def test_tensor_gram_bf16_storage(torch):
     assert st["wait_timeouts"] == 0
     for m in range(p.order):
         assert rel_err(tc[m][0], tc[m][1]) <= 2e-2, m
-        assert rel_err(tc[m][0], fma[m][0]) <= 1e-6, m
+        assert_factor_close(tc[m][0], fma[m][0], 1e-6, 1e-5, str(m))
 
 
 @pytest.mark.parametrize("c", [0.1, 1.0])
@@ -85,5 +85,38 @@ def test_epoch_tensor_gram(torch, c):
     g.epoch(c, seed=5)
     o.epoch(c, seed=5)
     for m in range(3):
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, str(m))
     assert g.stats()["wait_timeouts"] == 0
+
+
+def test_wait_timeout_is_reported_and_the_handle_recovers(torch):
+    """Test hook "test_gram_stall": block 0 of each tensor-core Gram launch
+    waits up to 20,000 SM cycles on an mbarrier phase that no MMA was committed
+    to, so its bounded wait gives up with nothing in flight.  The block frees its
+    tensor memory, writes no partial and is counted; the next synchronising call
+    reports the timeout once.  Afterwards the GPU and the library still work: a
+    fresh handle matches the oracle."""
+    from paper_2109_09534_gb300 import ntc
+    p = small_zipf()
+    split = dict(heavy_rows=128, chunk=700)
+    g, _ = pair(p, torch, gparams=dict(split, test_gram_stall=20000))
+    g.snmc(0, 0.1, seed=3)
+    assert g.stats()["wait_timeouts"] == 1
+    with pytest.raises(ntc.NTCError) as e:
+        g.sync()
+    assert e.value.status == ntc.NTC_ERR_CUDA and "gave up a bounded wait" in str(e.value)
+    g.sync()   # reported once per new timeout
+    g.ao_iter = 1
+    g.snmc(1, 0.1, seed=3)
+    with pytest.raises(ntc.NTCError) as e:
+        g.get_factor(1)
+    assert e.value.status == ntc.NTC_ERR_CUDA
+    g.close()
+    g2, o2 = pair(p, torch, gparams=split)
+    for m in range(3):
+        g2.ao_iter = 2
+        o2.ao_iter = 2
+        g2.snmc(m, 0.1, seed=9)
+        o2.snmc(m, 0.1, seed=9)
+        assert_factor_close(g2.get_factor(m), o2.get_factor(m), 1e-6, 1e-5, str(m))
+    assert g2.stats()["wait_timeouts"] == 0

@@ -190,3 +190,24 @@ def test_memory_model_bounds_a_running_job():
     assert used <= model, (used, model)
     assert used >= 0.25 * model, (used, model)
     srv.close()
+
+
+def test_job_with_a_gram_wait_timeout_fails():
+    """A served job whose epoch reports a tensor-core Gram wait that gave up
+    (forced by the "test_gram_stall" hook on a rank-32 job with split rows)
+    ends failed instead of taking its factors; a job submitted after the hook
+    is cleared runs normally."""
+    require_gpu()
+    spec = synth.JobSpec(0.0, [60, 50, 40], 32, 400_000, 0, 21)   # rows of mode 0 hold ~6,600 > 4096
+    p = synth.serving_job(spec, test_frac=0.02)
+    srv = ntc.Server(64e9, 4)
+    srv.set_param("test_gram_stall", 20000)
+    bad = submit(srv, 0, spec, p, max_epochs=2)
+    srv.set_param("test_gram_stall", 0)
+    good = submit(srv, 1, spec, p, max_epochs=2)
+    drain(srv, [bad, good])
+    assert srv.job_info(bad)["state"] == ntc.JOB_FAILED
+    info = srv.job_info(good)
+    assert info["state"] == ntc.JOB_DONE and info["epochs"] == 2 and info["rmse"] < info["rmse0"]
+    assert srv.stats()["failed"] == 1
+    srv.close()

@@ -46,6 +46,17 @@ def test_rmse_noalloc_matches_rmse():
     out = ctypes.c_double()
     assert f(g.h, idx2.shape[0], idx2.data_ptr(), val2.data_ptr(), ctypes.byref(out)) == ntc.NTC_OK
     assert out.value == pytest.approx(g.rmse(p.idx_train, p.val_train), rel=1e-4)
+    # an index out of range: NTC_ERR_INDEX, found on the device without
+    # reading a factor row; the next valid call starts from a clear flag
+    bad = p.idx_test.copy()
+    bad[17, 1] = p.dims[1]
+    bad[40, 2] = -1
+    bad_d = torch.from_numpy(np.ascontiguousarray(bad)).cuda()
+    assert f(g.h, bad_d.shape[0], bad_d.data_ptr(), val_d.data_ptr(), ctypes.byref(out)) == ntc.NTC_ERR_INDEX
+    assert b"out of range" in lib.ntc_last_error(g.h)
+    out = ctypes.c_double(-1.0)
+    assert f(g.h, idx_d.shape[0], idx_d.data_ptr(), val_d.data_ptr(), ctypes.byref(out)) == ntc.NTC_OK
+    assert out.value == pytest.approx(want, rel=1e-4)
     # beyond the fixed scratch: a clear error, nothing launched
     st = f(g.h, LIMIT + 1, idx_d.data_ptr(), val_d.data_ptr(), ctypes.byref(out))
     assert st == ntc.NTC_ERR_ARG
