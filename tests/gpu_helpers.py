@@ -45,6 +45,27 @@ def rel_err(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def max_row_err(a, b, floor_frac=1e-3):
+    """Largest per-row relative error max_r ||a_r - b_r|| / ||b_r|| over the
+    factor's rows, every row included (light and split alike).  A row whose
+    oracle norm is below floor_frac of the factor's RMS row norm (a row the
+    projection drove to or near zero) is measured against that floor instead,
+    so that the bound stays relative to the factor's scale."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b, axis=1)
+    rms = np.sqrt(np.mean(nb ** 2)) if nb.size else 0.0
+    den = np.maximum(nb, floor_frac * rms if rms > 0 else 1.0)
+    return float(np.max(np.linalg.norm(a - b, axis=1) / den)) if nb.size else 0.0
+
+
+def assert_factor_close(a, b, frob, row, what=""):
+    """Per-factor Frobenius bound and per-row bound (element-wise parity)."""
+    fe, re_ = rel_err(a, b), max_row_err(a, b)
+    assert fe <= frob, f"{what}: Frobenius relative error {fe:.3e} > {frob:g}"
+    assert re_ <= row, f"{what}: largest row relative error {re_:.3e} > {row:g}"
+
+
 def oracle_mask(idx, mode, dim, c, seed, ao_iter, inner):
     """Sample of every row of `mode` by the oracle, as a mask over bucket positions."""
     row_ptr, _ = oracle.bucket(idx, mode, dim)

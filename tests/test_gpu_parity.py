@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_2109_09534_gb300 import ntc, synth
 
-from gpu_helpers import oracle_mask, pair, rel_err, require_gpu, small_zipf
+from gpu_helpers import assert_factor_close, oracle_mask, pair, rel_err, require_gpu, small_zipf
 
 pytestmark = pytest.mark.gpu
 
@@ -93,7 +93,7 @@ def test_single_mode_update(torch, case, split):
         o.ao_iter = 3
         g.snmc(m, p.c, seed=99)
         o.snmc(m, p.c, seed=99)
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-6, m
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-6, 1e-5, f"{case} mode {m}")
 
 
 @pytest.mark.parametrize("max_inner", [1, 3])
@@ -106,7 +106,7 @@ def test_epoch_planted_cube(torch, max_inner, split):
     g.epoch(p.c, seed=4)
     o.epoch(p.c, seed=4)
     for m in range(p.order):
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, f"mode {m}")
     assert g.ao_iter == o.ao_iter == 10
 
 
@@ -116,7 +116,7 @@ def test_epoch_zipf_split_rows_and_mode_order(torch):
     g.epoch(0.2, seed=8, mode_order=[2, 0, 1])
     o.epoch(0.2, seed=8, mode_order=[2, 0, 1])
     for m in range(3):
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, f"mode {m}")
     st = g.stats()
     assert st["visits"] == o.visits and st["rows_skipped"] == o.rows_skipped
 
@@ -132,7 +132,7 @@ def test_warm_power_method_epochs(torch, rank):
         g.epoch(0.25, seed=50 + e)
         o.epoch(0.25, seed=50 + e)
     for m in range(3):
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, (rank, m)
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, str((rank, m)))
     # new observations reset the kept vectors on both sides: the first epoch
     # after them matches a cold run with the same iteration count
     g2, o2 = pair(p, torch, gparams=dict(power_iters=3, heavy_rows=256, chunk=300), oparams=dict(power_iters=3))
@@ -153,7 +153,7 @@ def test_ranks(torch, rank):
     g.epoch(0.25, seed=rank)
     o.epoch(0.25, seed=rank)
     for m in range(3):
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, (rank, m)
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, str((rank, m)))
 
 
 def test_bf16_storage_epoch(torch):
@@ -173,6 +173,18 @@ def test_predict_rmse_cost(torch):
     np.testing.assert_allclose(g.predict(p.idx_test), o.predict(p.idx_test), rtol=2e-5, atol=1e-6)
     assert g.rmse(p.idx_test, p.val_test) == pytest.approx(o.rmse(p.idx_test, p.val_test), rel=1e-4)
     assert g.cost() == pytest.approx(o.cost(), rel=1e-4)
+    # device-pointer queries: an index out of range gives NaN and reads no factor row
+    q = p.idx_test[:64].copy()
+    q[5, 0] = p.dims[0]
+    q[9, 2] = -3
+    qd = torch.from_numpy(q).cuda()
+    out = torch.empty(64, dtype=torch.float32, device="cuda")
+    g.predict_dev(64, qd.data_ptr(), out.data_ptr())
+    got = out.cpu().numpy()
+    assert np.isnan(got[5]) and np.isnan(got[9])
+    keep = np.ones(64, bool)
+    keep[[5, 9]] = False
+    np.testing.assert_allclose(got[keep], o.predict(q[keep]), rtol=2e-5, atol=1e-6)
 
 
 def test_init_factors_match_oracle_rule(torch):
@@ -183,7 +195,7 @@ def test_init_factors_match_oracle_rule(torch):
     o.set_observed(p.idx_train, p.val_train.astype(np.float64))
     o.init_factors(3)
     for m in range(3):
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-6
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-6, 1e-5)
 
 
 def test_deterministic_and_resumable(torch):
@@ -242,7 +254,7 @@ def test_error_statuses_leave_handle_usable(torch):
     g.epoch(0.1, seed=2)
     o.epoch(0.1, seed=2)
     for m in range(3):
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4)
 
 
 def test_edge_cases(torch):
@@ -272,7 +284,7 @@ def test_edge_cases(torch):
         g.epoch(c, seed=3)
         o.epoch(c, seed=3)
         for m in range(3):
-            assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, (c, m)
+            assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, str((c, m)))
 
 
 # ---- epoch-permutation sampling variant --------------------------------------------
@@ -316,7 +328,7 @@ def test_epoch_permutation_epoch_parity(torch, split):
         g.epoch(0.2, seed=31 + e)
         o.epoch(0.2, seed=31 + e)
     for m in range(3):
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, str(m))
 
 
 @pytest.mark.parametrize("overlap", [1, 2])
@@ -333,7 +345,7 @@ def test_light_rows_on_a_side_stream(torch, overlap):
         o.epoch(0.2, seed=61 + e)
     for m in range(3):
         np.testing.assert_array_equal(g.get_factor(m), g2.get_factor(m))
-        assert rel_err(g.get_factor(m), o.get_factor(m)) <= 1e-5, m
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, str(m))
 
 
 def test_pipelined_sampling_matches_stream_order(torch):
