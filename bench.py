@@ -3,14 +3,20 @@
 GB300: observed entries per second per AO epoch, and the fraction of the HBM
 roofline that the algorithmic-bytes model of the sampled visits reaches.
 
-Workload: a 10^4 x 10^4 x 10^4 tensor, rank 32, 100M observation draws whose
-indices follow Zipf(1.1) over a seeded row permutation in every mode, planted
-U[0, 1] factors, sigma = 0.01 Gaussian noise, 2% held out (98M train entries),
-minibatch fraction c = 0.1, MAX_INNER = 1, float32 factors.  One step is one
-epoch: ceil(1/c) = 10 AO iterations over the 3 modes (Sec. IV epoch).
+Workload (default): a 10^4 x 10^4 x 10^4 tensor, rank 32, 100M observation
+draws whose indices follow Zipf(1.1) over a seeded row permutation in every
+mode, planted U[0, 1] factors, sigma = 0.01 Gaussian noise, 2% held out (98M
+train entries), minibatch fraction c = 0.1, MAX_INNER = 1, float32 factors.
+One step is one epoch: ceil(1/c) = 10 AO iterations over the 3 modes (Sec. IV
+epoch).  --workload uniform4way: 10^5 x 5*10^4 x 2*10^4 x 10^3, R = 16, 200M
+uniform draws, Gamma(2, 0.5) factors, sigma = 0.05; --workload rating:
+10^6 x 5*10^5 x 200 user x item x time, R = 64, 500M draws (Zipf(1.2) users
+and items), values rounded to 1..5; each with --storage-bf16 for bfloat16
+factor storage, and --rmse-epochs E for the held-out RMSE of both storage
+forms after E epochs.
 
 --impl reference times the FP64 CPU oracle (OpenMP over rows, the paper's
-Algorithm 3 design) on the host cores instead.
+Algorithm 3 design) on the host cores instead: one whole epoch.
 """
 from __future__ import annotations
 
@@ -38,12 +44,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ntc", choices=["ntc", "reference"])
-    ap.add_argument("--nnz", type=int, default=100_000_000, help="observation draws (2%% held out)")
+    ap.add_argument("--nnz", type=int, default=0,
+                    help="observation draws (default: the workload's: 100M zipf, 200M uniform4way, 500M rating)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage-bf16", action="store_true")
-    ap.add_argument("--workload", default="zipf", choices=["zipf", "uber"],
-                    help="zipf: Zipf(1.1) 10^4-cube, R=32; uber: the Uber-shaped 4-way timing twin")
+    ap.add_argument("--workload", default="zipf", choices=["zipf", "uniform4way", "rating", "uber"],
+                    help="zipf: Zipf(1.1) 10^4-cube, R=32, 100M; uniform4way: 4-way R=16 200M uniform; rating: "
+                         "user x item x time R=64 500M; uber: the Uber-shaped 4-way timing twin")
+    ap.add_argument("--rmse-epochs", type=int, default=0,
+                    help="E > 0: held-out RMSE after E epochs from the initial factors with FP32 and with BF16 "
+                         "factor storage (same seeds), reported beside the throughput")
+    ap.add_argument("--cpu-sample", default="epoch", choices=["epoch", "iteration"],
+                    help="CPU baseline sample: one whole epoch (default) or one AO iteration (all modes once)")
+    ap.add_argument("--ref-epochs", type=int, default=1,
+                    help="--impl reference: whole epochs timed (the requested --steps are not all run: an "
+                         "epoch of the FP64 oracle takes minutes; the line says so)")
     ap.add_argument("--rank", type=int, default=0, help="fitted rank (default: the workload's)")
     ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2],
                     help="light rows on a second stream: 2 beside the split-row Gram (default), 1 beside the "
@@ -74,9 +90,21 @@ def parse():
     return ap.parse_args()
 
 
+DEFAULT_NNZ = {"zipf": 100_000_000, "uniform4way": 200_000_000, "rating": 500_000_000, "uber": 3_309_490}
+
+
 def workload(args):
     from paper_2109_09534_gb300 import synth
-    p = synth.uber_twin() if args.workload == "uber" else synth.zipf_1e4cube(nnz_total=args.nnz)
+    n = args.nnz or DEFAULT_NNZ[args.workload]
+    args.nnz = n
+    if args.workload == "uber":
+        p = synth.uber_twin()
+    elif args.workload == "uniform4way":
+        p = synth.uniform_4way(nnz_total=n)
+    elif args.workload == "rating":
+        p = synth.rating_3way(nnz_total=n)
+    else:
+        p = synth.zipf_1e4cube(nnz_total=n)
     if args.rank:
         p.rank = args.rank
     return p
@@ -91,6 +119,17 @@ def config(p, args):
         text = (f"uber-shaped 183x24x1140x1717 tensor, 3,309,490 uniform draws of a planted rank-10 "
                 f"noiseless tensor ({p.nnz} train), fitted R={p.rank}, c=0.5, MAX_INNER=1, {storage} factor storage")
         l2 = "inputs larger than L2: 4 per-mode buckets of 16 B/entry (0.21 GB) re-read every epoch"
+    elif args.workload == "uniform4way":
+        text = (f"uniform 4-way 100000x50000x20000x1000 tensor, R={p.rank}, {args.nnz // 1_000_000}M uniform draws "
+                f"({p.nnz} train), planted Gamma(2, 0.5) factors, sigma=0.05, c=0.1, MAX_INNER=1, "
+                f"{storage} factor storage")
+        l2 = "inputs larger than L2: 4 per-mode buckets of 16 B/entry (~12.5 GB) re-read every epoch"
+    elif args.workload == "rating":
+        text = (f"rating-shaped user x item x time 1000000x500000x200 tensor, R={p.rank}, "
+                f"{args.nnz // 1_000_000}M draws ({p.nnz} train; Zipf(1.2) users and items, uniform time), "
+                f"planted U[0, 2a] factors, values rounded and clamped to 1..5, c=0.1, MAX_INNER=1, "
+                f"{storage} factor storage")
+        l2 = "inputs larger than L2: 3 per-mode buckets of 16 B/entry (~23.8 GB) re-read every epoch"
     else:
         text = (f"zipf1.1 10000^3 tensor, R={p.rank}, {args.nnz // 1_000_000}M draws ({p.nnz} train), c=0.1, "
                 f"MAX_INNER=1, {storage} factor storage")
@@ -240,12 +279,13 @@ def replica_value(units_per_rank, ws, ms_local):
     return ws * units_per_rank / (ms * 1e-3), ms
 
 
-def cpu_baseline(p, steps=1, warmup=0):
+def cpu_baseline(p, epochs=1, warmup=0, sample="epoch"):
     """The FP64 oracle as it stands, OpenMP over rows (the paper's Algorithm 3),
-    on the host cores.  Bounded sample: one call of Algorithm 1 on mode 0 of the
-    full workload; an epoch is 3 modes x 10 AO iterations of such calls (the
-    three modes are statistically identical here), so the epoch time is
-    estimated as 30x the sampled call."""
+    on the host cores.  sample="epoch": `epochs` whole epochs (ceil(1/c) AO
+    iterations over every mode) are timed, after `warmup` single Algorithm-1
+    calls; sample="iteration": one AO iteration (every mode once) is timed and
+    the epoch is that times ceil(1/c) (each AO iteration does the same work).
+    Returns (the cpu_baseline object, the timed seconds per epoch)."""
     import numpy as np
 
     import oracle
@@ -254,41 +294,50 @@ def cpu_baseline(p, steps=1, warmup=0):
     o.init_factors(3)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     cores = int(os.environ.get("OMP_NUM_THREADS", cores))
-    if p.nnz <= 10_000_000:   # small workload: whole epochs
-        times = []
-        for s in range(warmup + steps):
-            t0 = time.perf_counter()
-            o.epoch(p.c, seed=4 + s)
-            if s >= warmup:
-                times.append(time.perf_counter() - t0)
-        t_epoch = statistics.median(times)
-        return {"value": p.nnz / t_epoch, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": f"whole epochs of the {p.nnz}-entry workload, {t_epoch:.2f} s median of {steps}"}, times
+    T = int(np.ceil(1.0 / p.c - 1e-12))
+    N = len(p.dims)
     for w in range(warmup):
         o.ao_iter = 1000 + w
-        o.snmc(0, p.c, seed=4)
-    times = []
-    for s in range(steps):
-        o.ao_iter = s
+        o.snmc(w % N, p.c, seed=3)
+    o.ao_iter = 0
+    if sample == "iteration":
         t0 = time.perf_counter()
-        o.snmc(0, p.c, seed=4)
+        for m in range(N):
+            o.snmc(m, p.c, seed=4)
+        t_iter = time.perf_counter() - t0
+        t_epoch = t_iter * T
+        text = (f"one AO iteration (Algorithm 1 on each of the {N} modes) of the full {p.nnz}-entry workload, "
+                f"{t_iter:.2f} s; epoch = {T} such iterations")
+        return {"value": p.nnz / t_epoch, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text}, [t_epoch]
+    times = []
+    for s in range(epochs):
+        t0 = time.perf_counter()
+        o.epoch(p.c, seed=4 + s)
         times.append(time.perf_counter() - t0)
-    calls = len(p.dims) * int(np.ceil(1.0 / p.c - 1e-12))
-    t_epoch = statistics.median(times) * calls
-    return {"value": p.nnz / t_epoch, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one Algorithm-1 call (mode 0, c={p.c}) on the full {p.nnz}-entry workload, "
-                      f"{statistics.median(times):.2f} s median of {steps}; epoch = {calls} such calls"}, times
+    t_epoch = statistics.median(times)
+    text = (f"whole epoch{'s' if epochs > 1 else ''} ({T} AO iterations x {N} modes) of the full {p.nnz}-entry "
+            f"workload, {t_epoch:.2f} s{' median of %d' % epochs if epochs > 1 else ''}"
+            + (f"; warm-up: {warmup} single Algorithm-1 calls" if warmup else ""))
+    return {"value": p.nnz / t_epoch, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text}, times
 
 
 def run_reference(args):
+    """The reference arm: the paper ships no code, so the FP64 oracle (the
+    paper's OpenMP design) is timed on the host cores, on the same workload.
+    Its epochs take minutes, so it times --ref-epochs whole epochs after
+    --warmup single Algorithm-1 calls, and the line reports what was timed."""
     ws, rank, _ = dist()
     if rank != 0:
         return
     p = workload(args)
-    cb, times = cpu_baseline(p, steps=args.steps, warmup=args.warmup)
+    cb, times = cpu_baseline(p, epochs=args.ref_epochs, warmup=args.warmup, sample=args.cpu_sample)
     v = cb["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": p.nnz / v * 1e3,
+            "steps": len(times), "steps_requested": args.steps, "warmup": args.warmup,
+            "warmup_unit": "one Algorithm-1 call (one mode update)", "ms_per_step": p.nnz / v * 1e3,
+            "timed_s": sum(times),
+            "steps_note": (f"one step = one whole epoch of the FP64 oracle ({len(times)} timed; the "
+                           f"{args.steps} requested would take about {args.steps * p.nnz / v / 60:.0f} min)"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(p, args), "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -432,12 +481,34 @@ def run_ntc(args):
                              "ncu launch list)") if args.overlap else
                             "CUDA-event times per kernel class; split-row sampling runs beside the Gram",
             "visits_per_s": ws * visits / (ms * 1e-3)}
+    if args.rmse_epochs > 0:
+        line["heldout_rmse"] = storage_rmse(p, args, stream.cuda_stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         del g
         torch.cuda.empty_cache()
-        line["cpu_baseline"], _ = cpu_baseline(p, steps=1)
+        line["cpu_baseline"], _ = cpu_baseline(p, epochs=1, sample=args.cpu_sample)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def storage_rmse(p, args, stream):
+    """Held-out RMSE after args.rmse_epochs epochs from the initial factors,
+    FP32 and BF16 factor storage on the same seeds (the precision contract:
+    BF16 storage within 1% of FP32)."""
+    from paper_2109_09534_gb300 import ntc
+    out = {}
+    for bf in (0, 1):
+        g = ntc.NTC(p.dims, p.rank, p.lam, stream=stream, storage_bf16=bf, gram_tc=args.gram_tc)
+        g.set_observed(p.idx_train, p.val_train)
+        r0 = g.rmse(p.idx_test, p.val_test)
+        for e in range(args.rmse_epochs):
+            g.epoch(p.c, seed=500 + e)
+        out["bf16" if bf else "fp32"] = g.rmse(p.idx_test, p.val_test)
+        out["initial"] = r0
+        g.close()
+    out["epochs"] = args.rmse_epochs
+    out["bf16_vs_fp32"] = out["bf16"] / out["fp32"] - 1.0
+    return out
 
 
 def run_serve(args):
