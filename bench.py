@@ -64,9 +64,10 @@ def parse():
     ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2],
                     help="light rows on a second stream: 2 beside the split-row Gram (default), 1 beside the "
                          "sampler, 0 stream order")
-    ap.add_argument("--gram-tc", type=int, default=1, choices=[0, 1],
-                    help="1: split-row Gram on the tensor cores where the shape has a kernel (R_pad = 32, "
-                         "orders 2-4; default); 0: FP32 FMA")
+    ap.add_argument("--gram-tc", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="split-row Gram where the shape has a tensor-core kernel (R_pad = 32, orders 2-4): "
+                         "1 tensor cores, rows gathered into registers (default); 2 tensor cores, rows gathered "
+                         "by TMA gather4 in a warp-specialised pipeline; 0: FP32 FMA")
     ap.add_argument("--sampler", default="independent", choices=["independent", "perm"],
                     help="perm: epoch-permutation minibatches (labelled variant)")
     ap.add_argument("--power-warm", type=int, default=0,
@@ -140,6 +141,8 @@ def config(p, args):
         text += ", light rows in stream order"
     if getattr(args, "gram_tc", 1) == 0:
         text += ", split-row Gram on FP32 FMA"
+    elif getattr(args, "gram_tc", 1) == 2:
+        text += ", split-row Gram on the tensor cores with TMA gather4 row loads"
     if getattr(args, "sampler", "independent") == "perm":
         text += ", variant: epoch-permutation minibatches (disjoint stretches of one permutation per row and epoch)"
     return {"workload": text, "dims": p.dims, "rank": p.rank, "nnz_train": p.nnz, "c": p.c, "lambda": p.lam,
@@ -169,7 +172,7 @@ def tf32_peak():
 
 # sources of the epoch kernels (the serving runtime and the host API are not
 # part of what the DRAM counters measured)
-KERNEL_SOURCES = ("ntc_internal.cuh", "nmc_kernels.cuh", "gram_tc.cuh", "launch_rp.cuh",
+KERNEL_SOURCES = ("ntc_internal.cuh", "nmc_kernels.cuh", "gram_tc.cuh", "gram_tma.cuh", "launch_rp.cuh",
                   "nmc_rp8.cu", "nmc_rp16.cu", "nmc_rp32.cu", "nmc_rp64.cu")
 
 
@@ -413,7 +416,7 @@ def run_ntc(args):
     R, N = p.rank, p.order
     # the tensor-core Gram runs at padded rank 32 (16 < R <= 32) and orders 2-4
     tensor_gram = bool(args.gram_tc) and 16 < R <= 32 and N <= 4
-    gram_name = "k_heavy_gram_tc" if tensor_gram else "k_heavy_gram"
+    gram_name = ("k_heavy_gram_tma" if args.gram_tc in (2, 3) else "k_heavy_gram_tc") if tensor_gram else "k_heavy_gram"
     kname = {"light": "k_light", "heavy_sample": "k_heavy_sample", "heavy_resolve": "k_heavy_resolve",
              "heavy_gram": gram_name, "finish": "k_rows_finish"}[dom]
     total_k = sum(v["ms"] for v in prof.values())

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "gram_tc.cuh"
+#include "gram_tma.cuh"
 #include "nmc_kernels.cuh"
 #include "ntc_host.h"
 
@@ -18,6 +19,16 @@ constexpr bool kTensorGram = RP == 32 && EW == 4 && NOR > 0;
 constexpr int kTcTile = 64;
 constexpr int kTcWindow = 1;   // tiles per tensor-memory accumulation window
 constexpr int kTcThreads = 128;
+// TMA-gather form ("gram_tc" 2): row stages in flight per block (the gathered
+// rows of a stage take NOR * 8 KB at float32) and blocks per SM
+template <int NOR>
+constexpr int kTmaStages = NOR == 3 ? 2 : 4;
+constexpr int kTmaBlocks = 2;
+template <int EW, bool BF, int NOR>
+using TmaG = GramTMA<EW, BF, NOR, kTcTile, kTmaStages<NOR>>;
+// ("gram_tc" 3: two stages, three blocks per SM)
+template <int EW, bool BF, int NOR>
+using TmaG3 = GramTMA<EW, BF, NOR, kTcTile, 2>;
 
 template <int RP, int EW, bool BF, int NOR>
 cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, bool mask_only) {
@@ -30,8 +41,14 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         cudaError_t e = set_smem(k_light<RP, EW, BF, NOR>, LightSmem<RP, EW, BF, NOR>::bytes(nomax));
         if (e == cudaSuccess) e = set_smem(k_heavy_gram<RP, EW, BF, NOR>, HeavyGramSmem<RP, EW, BF, NOR>::bytes(nomax));
         if (e == cudaSuccess) e = set_smem(k_rows_finish<RP>, RowFinish<RP>::bytes());
-        if constexpr (kTensorGram<RP, EW, NOR>)
+        if constexpr (kTensorGram<RP, EW, NOR>) {
             if (e == cudaSuccess) e = set_smem(k_heavy_gram_tc<EW, BF, NOR, kTcTile, kTcWindow, kTcThreads>, GramTC<EW, kTcTile, kTcWindow, kTcThreads>::BYTES);
+            if (e == cudaSuccess)
+                e = set_smem(k_heavy_gram_tma<EW, BF, NOR, kTcTile, kTmaStages<NOR>, kTmaBlocks>, TmaG<EW, BF, NOR>::BYTES);
+            if (e == cudaSuccess)
+                e = set_smem(k_heavy_gram_tma<EW, BF, NOR, kTcTile, 2, 3>, TmaG3<EW, BF, NOR>::BYTES);
+
+        }
         attr_err = e;
     });
     if (attr_err != cudaSuccess) return attr_err;
@@ -106,10 +123,22 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
             ++*L.launches;
             if (pipe && (e = cudaEventRecord(h->ev_free[a.sset], s)) != cudaSuccess) return e;
         } else {
+            const GatherMaps* gm = nullptr;
+            if constexpr (kTensorGram<RP, EW, NOR>)
+                if (h->gram_tc >= 2 && (e = gather_maps(h, (int)a.ss.mode, &gm)) != cudaSuccess) return e;
             e = L.run(NTC_K_HEAVY_GRAM, p.visits_heavy * L.bpv, [&] {
                 bool tensor = false;
                 if constexpr (kTensorGram<RP, EW, NOR>) {
-                    if (h->gram_tc) {
+                    if (h->gram_tc == 2) {
+                        using T = TmaG<EW, BF, NOR>;
+                        k_heavy_gram_tma<EW, BF, NOR, kTcTile, kTmaStages<NOR>, kTmaBlocks>
+                            <<<p.n_chunks + p.n_heavy, T::NT, T::BYTES, s>>>(a, *gm);
+                        tensor = true;
+                    } else if (h->gram_tc == 3) {
+                        using T = TmaG3<EW, BF, NOR>;
+                        k_heavy_gram_tma<EW, BF, NOR, kTcTile, 2, 3><<<p.n_chunks + p.n_heavy, T::NT, T::BYTES, s>>>(a, *gm);
+                        tensor = true;
+                    } else if (h->gram_tc) {
                         using T = GramTC<EW, kTcTile, kTcWindow, kTcThreads>;
                         k_heavy_gram_tc<EW, BF, NOR, kTcTile, kTcWindow, kTcThreads><<<p.n_chunks + p.n_heavy, T::NT, T::BYTES, s>>>(a);
                         tensor = true;

@@ -702,6 +702,54 @@ ntc_status prepare_epoch(ntc_handle* h, double c) {
     return reset_stats(h);
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library links only the CUDA runtime).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+cudaError_t gather_maps(ntc_handle* h, int mode, const GatherMaps** out) {
+    const int want = h->storage_bf16 ? 2 : 1;
+    if (h->gmaps_state[mode] != want) {
+        EncodeTiled enc = encode_tiled();
+        if (!enc) return cudaErrorNotSupported;
+        int o = 0;
+        for (int i = 0; i < h->order; ++i) {
+            if (i == mode) continue;
+            if (o >= 3) return cudaErrorInvalidValue;
+            void* base = h->storage_bf16 ? h->Ub[i].p : h->U[i].p;
+            const cuuint64_t dims[2] = {(cuuint64_t)h->rp, (cuuint64_t)h->dims[i]};
+            const cuuint64_t strides[1] = {(cuuint64_t)h->rp * (h->storage_bf16 ? 2u : 4u)};
+            const cuuint32_t box[2] = {(cuuint32_t)h->rp, 1u};
+            const cuuint32_t es[2] = {1u, 1u};
+            const CUresult r = enc(&h->gmaps[mode].m[o], h->storage_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                   2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+            ++o;
+        }
+        h->gmaps_state[mode] = want;
+    }
+    *out = &h->gmaps[mode];
+    return cudaSuccess;
+}
+
 cudaError_t fault_count_enqueue(ntc_handle* h, unsigned long long* host) {
     if (!h->stat.p) {
         *host = 0;
@@ -856,7 +904,9 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
         if (v != 0.0 && v != 1.0) return fail(h, NTC_ERR_ARG, "sampler must be 0 (independent) or 1 (epoch permutation)");
         h->sampler = (int)v;
     } else if (k == "gram_tc") {
-        h->gram_tc = v != 0.0 ? 1 : 0;
+        if (!(v == 0.0 || v == 1.0 || v == 2.0 || v == 3.0))
+            return fail(h, NTC_ERR_ARG, "gram_tc must be 0, 1, 2 or 3");
+        h->gram_tc = (int)v;
     } else if (k == "test_gram_stall") {
         if (!(v >= 0 && v <= 1e9)) return fail(h, NTC_ERR_ARG, "test_gram_stall must be in [0, 1e9] cycles");
         h->test_stall_cycles = (long long)v;

@@ -8,6 +8,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/ntc.h"
 #include "ntc_internal.cuh"
 
@@ -56,6 +58,12 @@ struct ModePlan {
 };
 
 inline int pad_rank(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
+
+// TMA descriptors of the other modes' factor matrices for the row gathers of
+// one mode update (gram_tma.cuh reads them as a kernel parameter).
+struct GatherMaps {
+    CUtensorMap m[3];
+};
 
 }  // namespace ntc
 
@@ -106,6 +114,10 @@ struct ntc_handle {
     // to the caller; test hook that makes block 0 of each such launch give up
     unsigned long long faults_seen = 0;
     long long test_stall_cycles = 0;
+    // TMA descriptors of the row gathers, per updated mode, encoded on first use
+    // (factor buffers never move after ntc_create / storage_bf16)
+    ntc::GatherMaps gmaps[ntc::kMaxOrder];
+    int gmaps_state[ntc::kMaxOrder] = {};   // 0 none, 1 float32 masters, 2 bfloat16 copies
     uint64_t upd = 0;                       // mode updates launched so far
     cudaStream_t samp = nullptr;            // split-row sampling stream
     cudaEvent_t ev_sampled[2] = {}, ev_free[2] = {};
@@ -214,6 +226,9 @@ int64_t handle_device_bytes(const ntc_handle* h);
 // Builds every mode's plan for minibatch fraction c and sizes the epoch
 // scratch, so that the first ntc_epoch at c allocates nothing.
 ntc_status prepare_epoch(ntc_handle* h, double c);
+// The row-gather descriptors of mode `mode` for the handle's current storage
+// (encoded once and cached in the handle).
+cudaError_t gather_maps(ntc_handle* h, int mode, const GatherMaps** out);
 // Enqueues on the handle's stream a copy of the number of tensor-core Gram
 // blocks that have given up a bounded wait since the handle was created into
 // *host (pinned host memory); 0 if the handle has not run an update.

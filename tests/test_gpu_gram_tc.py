@@ -45,30 +45,34 @@ def one_update(p, torch, gram_tc, split, c=0.1, bf16=False):
     return out, st
 
 
+@pytest.mark.parametrize("gram_tc", [1, 2], ids=["regrows", "tmagather"])
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("split", list(SPLITS))
-def test_single_update_tensor_gram(torch, case, split):
-    """FP32 factors after one mode update: tensor-core Gram vs FP64 within 1e-6."""
+def test_single_update_tensor_gram(torch, case, split, gram_tc):
+    """FP32 factors after one mode update: tensor-core Gram (rows gathered into
+    registers, or by TMA gather4 in the warp-specialised form) vs FP64 within 1e-6."""
     p = CASES[case]()
-    got, st = one_update(p, torch, 1, split)
+    got, st = one_update(p, torch, gram_tc, split)
     assert st["visits_heavy"] > 0 and st["wait_timeouts"] == 0
     for m, (a, want) in enumerate(got):
         assert_factor_close(a, want, 1e-6, 1e-5, str((case, split, m, rel_err(a, want))))
 
 
-@pytest.mark.parametrize("case", ["zipf2k_r32", "order4_r32"])
-def test_tensor_gram_matches_fma_gram(torch, case):
-    """The two Gram paths of one handle agree to FP32 rounding."""
+@pytest.mark.parametrize("gram_tc", [1, 2], ids=["regrows", "tmagather"])
+@pytest.mark.parametrize("case", ["zipf2k_r32", "order4_r32", "order2_r32"])
+def test_tensor_gram_matches_fma_gram(torch, case, gram_tc):
+    """The tensor-core and FP32 FMA Gram paths of one handle agree to FP32 rounding."""
     p = CASES[case]()
-    tc, _ = one_update(p, torch, 1, "small")
+    tc, _ = one_update(p, torch, gram_tc, "small")
     fma, _ = one_update(p, torch, 0, "small")
     for m in range(p.order):
         assert_factor_close(tc[m][0], fma[m][0], 1e-6, 1e-5, str(m))
 
 
-def test_tensor_gram_bf16_storage(torch):
+@pytest.mark.parametrize("gram_tc", [1, 2], ids=["regrows", "tmagather"])
+def test_tensor_gram_bf16_storage(torch, gram_tc):
     p = CASES["zipf2k_r32"]()
-    tc, st = one_update(p, torch, 1, "small", bf16=True)
+    tc, st = one_update(p, torch, gram_tc, "small", bf16=True)
     fma, _ = one_update(p, torch, 0, "small", bf16=True)
     assert st["wait_timeouts"] == 0
     for m in range(p.order):
@@ -76,12 +80,13 @@ def test_tensor_gram_bf16_storage(torch):
         assert_factor_close(tc[m][0], fma[m][0], 1e-6, 1e-5, str(m))
 
 
+@pytest.mark.parametrize("gram_tc", [1, 2], ids=["regrows", "tmagather"])
 @pytest.mark.parametrize("c", [0.1, 1.0])
-def test_epoch_tensor_gram(torch, c):
+def test_epoch_tensor_gram(torch, c, gram_tc):
     """One epoch at c = 0.1 (10 AO iterations) and one full-gradient AO
     iteration at c = 1 (every visit of a split row, the longest blocks)."""
     p = small_zipf()
-    g, o = pair(p, torch, gparams=dict(heavy_rows=128, gram_tc=1))
+    g, o = pair(p, torch, gparams=dict(heavy_rows=128, gram_tc=gram_tc))
     g.epoch(c, seed=5)
     o.epoch(c, seed=5)
     for m in range(3):
@@ -89,7 +94,8 @@ def test_epoch_tensor_gram(torch, c):
     assert g.stats()["wait_timeouts"] == 0
 
 
-def test_wait_timeout_is_reported_and_the_handle_recovers(torch):
+@pytest.mark.parametrize("gram_tc", [1, 2], ids=["regrows", "tmagather"])
+def test_wait_timeout_is_reported_and_the_handle_recovers(torch, gram_tc):
     """Test hook "test_gram_stall": block 0 of each tensor-core Gram launch
     waits up to 20,000 SM cycles on an mbarrier phase that no MMA was committed
     to, so its bounded wait gives up with nothing in flight.  The block frees its
@@ -99,7 +105,7 @@ def test_wait_timeout_is_reported_and_the_handle_recovers(torch):
     from paper_2109_09534_gb300 import ntc
     p = small_zipf()
     split = dict(heavy_rows=128, chunk=700)
-    g, _ = pair(p, torch, gparams=dict(split, test_gram_stall=20000))
+    g, _ = pair(p, torch, gparams=dict(split, gram_tc=gram_tc, test_gram_stall=20000))
     g.snmc(0, 0.1, seed=3)
     assert g.stats()["wait_timeouts"] == 1
     with pytest.raises(ntc.NTCError) as e:
@@ -112,7 +118,7 @@ def test_wait_timeout_is_reported_and_the_handle_recovers(torch):
         g.get_factor(1)
     assert e.value.status == ntc.NTC_ERR_CUDA
     g.close()
-    g2, o2 = pair(p, torch, gparams=split)
+    g2, o2 = pair(p, torch, gparams=dict(split, gram_tc=gram_tc))
     for m in range(3):
         g2.ao_iter = 2
         o2.ao_iter = 2
