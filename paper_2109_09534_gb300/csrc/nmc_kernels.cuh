@@ -938,6 +938,8 @@ __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan
     int nsel = 0, ncand = 0;
     for (uint32_t base = pb & ~3u; base < pe; base += kThreads * kSamplePer) {
         const uint32_t q0 = base + threadIdx.x * kSamplePer;
+        // only the first and the last round of a chunk hold positions outside it
+        const bool edge = base < pb || base + kThreads * kSamplePer > pe;
         uint32_t kv[kSamplePer];
 #pragma unroll
         for (int b = 0; b < kSamplePer / 4; ++b) {
@@ -952,7 +954,7 @@ __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan
         unsigned dm = 0u, cm = 0u;
 #pragma unroll
         for (int j = 0; j < kSamplePer; ++j) {
-            const bool in = q0 + j >= pb && q0 + j < pe;
+            const bool in = !edge || (q0 + j >= pb && q0 + j < pe);
             const bool d = in && (lo_all || kv[j] < lo);
             const bool cn = in && !d && (hi_all || kv[j] < hi);
             dm |= (unsigned)d << j;

@@ -211,3 +211,38 @@ def test_job_with_a_gram_wait_timeout_fails():
     assert info["state"] == ntc.JOB_DONE and info["epochs"] == 2 and info["rmse"] < info["rmse0"]
     assert srv.stats()["failed"] == 1
     srv.close()
+
+
+@pytest.mark.parametrize("epochs", [1, 2])
+def test_served_job_in_a_mix_matches_the_oracle(epochs):
+    """A small job served beside three others (epochs of different jobs
+    interleaved tick by tick) against the FP64 oracle run from the same initial
+    factors (drawn by the oracle's rule, rounded to float32 as the device stores
+    them) with the same per-epoch seeds: within 1e-5 (Frobenius) and 1e-4 (per
+    row) relative after each of its epochs."""
+    require_gpu()
+    import oracle
+
+    from gpu_helpers import assert_factor_close
+    jobs = small_jobs()
+    srv = ntc.Server(64e9, 8)
+    srv.set_param("max_enqueue_per_step", 1)
+    target_k = 0   # the 3-way rank-8 FP32 job
+    ids = []
+    for k, (s, p) in enumerate(jobs):
+        ids.append(submit(srv, k, s, p, max_epochs=epochs if k == target_k else 3))
+    drain(srv, ids)
+    assert srv.stats()["failed"] == 0
+    s, p = jobs[target_k]
+    assert s.storage_bf16 == 0
+    o = oracle.Oracle(p.dims, p.rank, p.lam)
+    o.set_observed(p.idx_train, p.val_train.astype(np.float64))
+    o.init_factors(7)
+    for m in range(len(p.dims)):
+        o.set_factor(m, o.get_factor(m).astype(np.float32).astype(np.float64))
+    for e in range(epochs):
+        o.epoch(p.c, seed=SEED0 + target_k + e)
+    got = factors_of(srv, ids[target_k], p)
+    for m in range(len(p.dims)):
+        assert_factor_close(got[m], o.get_factor(m), 1e-5, 1e-4, f"mode {m} after {epochs} epochs")
+    srv.close()
