@@ -8,6 +8,7 @@
 #include "gram_tma.cuh"
 #include "nmc_kernels.cuh"
 #include "ntc_host.h"
+#include "tiny_rows.cuh"
 
 namespace ntc {
 
@@ -41,6 +42,8 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         cudaError_t e = set_smem(k_light<RP, EW, BF, NOR>, LightSmem<RP, EW, BF, NOR>::bytes(nomax));
         if (e == cudaSuccess) e = set_smem(k_heavy_gram<RP, EW, BF, NOR>, HeavyGramSmem<RP, EW, BF, NOR>::bytes(nomax));
         if (e == cudaSuccess) e = set_smem(k_rows_finish<RP>, RowFinish<RP>::bytes());
+        if constexpr (EW == 4 && NOR > 0)
+            if (e == cudaSuccess) e = set_smem(k_tiny_rows<RP, EW, BF, NOR>, TinyShape<RP>::bytes());
         if constexpr (kTensorGram<RP, EW, NOR>) {
             if (e == cudaSuccess) e = set_smem(k_heavy_gram_tc<EW, BF, NOR, kTcTile, kTcWindow, kTcThreads>, GramTC<EW, kTcTile, kTcWindow, kTcThreads>::BYTES);
             if (e == cudaSuccess)
@@ -52,7 +55,7 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         attr_err = e;
     });
     if (attr_err != cudaSuccess) return attr_err;
-    const bool fork = p.n_light > 0 && p.n_heavy > 0 && L.h->overlap;
+    const bool fork = p.n_light + p.n_tiny > 0 && p.n_heavy > 0 && L.h->overlap;
     // light rows: in stream order, or on the side stream (forked here for
     // overlap 1, beside the split-row sampler; after the sampler for overlap
     // 2, beside the split-row Gram)
@@ -68,11 +71,19 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
             if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
         }
-        if (p.n_light > 0) {
-            const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv;
+        if (p.n_light + p.n_tiny > 0) {
+            const int64_t bytes = (p.visits - p.visits_heavy) * L.bpv;   // light and one-warp rows
             cudaStream_t ls = fork ? L.h->side : s;
             e = L.run_on(ls, NTC_K_LIGHT, mask_only ? 0 : bytes, [&] {
-                k_light<RP, EW, BF, NOR><<<p.n_light, kLightThreads, LightSmem<RP, EW, BF, NOR>::bytes(a.n_other), ls>>>(a);
+                if constexpr (EW == 4 && NOR > 0) {
+                    if (p.n_tiny > 0) {
+                        constexpr int W = TinyShape<RP>::WARPS;
+                        k_tiny_rows<RP, EW, BF, NOR><<<(p.n_tiny + W - 1) / W, W * 32, TinyShape<RP>::bytes(), ls>>>(a);
+                        if (p.n_light > 0) ++*L.launches;
+                    }
+                }
+                if (p.n_light > 0)
+                    k_light<RP, EW, BF, NOR><<<p.n_light, kLightThreads, LightSmem<RP, EW, BF, NOR>::bytes(a.n_other), ls>>>(a);
             });
             if (e != cudaSuccess) return e;
             if (fork && (e = cudaEventRecord(L.h->ev_join, ls)) != cudaSuccess) return e;

@@ -15,6 +15,7 @@
 
 #include "aux_kernels.cuh"
 #include "ntc_host.h"
+#include "tiny_rows.cuh"
 
 using namespace ntc;
 
@@ -60,13 +61,14 @@ int partial_width(int rp) {
 // ---- per-(mode, c) plan ------------------------------------------------------
 ntc_status build_plan(ntc_handle* h, int mode, double c) {
     ModePlan& p = h->plan[mode];
+    const bool tiny = h->tiny_rows && ew_of(h->order) == 4;
     if (p.valid && p.c == c && p.heavy_threshold == h->heavy_threshold && p.chunk == h->chunk &&
-        p.bracket_z == h->bracket_z)
+        p.bracket_z == h->bracket_z && p.tiny == tiny)
         return NTC_OK;
     p.valid = false;
     const std::vector<int64_t>& rp = h->row_ptr_h[mode];
     const int64_t P = h->dims[mode];
-    std::vector<std::pair<int64_t, int32_t>> light;   // (n, row)
+    std::vector<std::pair<int64_t, int32_t>> light, tinyv;   // (n, row)
     std::vector<int32_t> light_k;
     std::vector<int4> chunks, caps, heavy, hcand, groups;
     std::vector<int32_t> voff;   // epoch-permutation variant: chunk list starts
@@ -90,7 +92,8 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
         ++updated;
         visits += k;
         if (n <= h->heavy_threshold) {
-            light.push_back({n, (int32_t)r});
+            if (tiny && n <= kTinyMax) tinyv.push_back({n, (int32_t)r});
+            else light.push_back({n, (int32_t)r});
             continue;
         }
         visits_heavy += k;
@@ -147,6 +150,12 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
         lrows[i] = light[i].second;
         light_k[i] = (int32_t)std::floor(c * (double)light[i].first);
     }
+    // rows of one warp each, in the same order (longest first)
+    std::vector<int32_t> trows(tinyv.size()), tk(tinyv.size());
+    for (size_t i = 0; i < tinyv.size(); ++i) {
+        trows[i] = tinyv[i].second;
+        tk[i] = (int32_t)std::floor(c * (double)tinyv[i].first);
+    }
     if (cand_total >= (1ll << 31) || extra_total >= (1ll << 31))
         return fail(h, NTC_ERR_ARG, "sampler bracket too wide for this row size");
     auto up = [&](DevMem& m, const void* src, size_t bytes) -> cudaError_t {
@@ -156,6 +165,8 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     };
     NTC_CUDA(h, up(p.light_rows, lrows.data(), lrows.size() * 4));
     NTC_CUDA(h, up(p.light_k, light_k.data(), light_k.size() * 4));
+    NTC_CUDA(h, up(p.tiny_rows, trows.data(), trows.size() * 4));
+    NTC_CUDA(h, up(p.tiny_k, tk.data(), tk.size() * 4));
     NTC_CUDA(h, up(p.chunks, chunks.data(), chunks.size() * sizeof(int4)));
     NTC_CUDA(h, up(p.vis_off, voff.data(), voff.size() * sizeof(int32_t)));
     NTC_CUDA(h, up(p.chunk_caps, caps.data(), caps.size() * sizeof(int4)));
@@ -174,6 +185,8 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     p.rows_updated = updated;
     p.rows_skipped = skipped;
     p.n_light = (int)light.size();
+    p.n_tiny = (int)tinyv.size();
+    p.tiny = tiny;
     p.n_heavy = (int)heavy.size();
     p.n_chunks = (int)chunks.size();
     p.n_groups = (int)groups.size();
@@ -232,6 +245,9 @@ ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t a
     a.ss.k1 = (uint32_t)(seed >> 32);
     a.light_rows = p.light_rows.as<int32_t>();
     a.light_k = p.light_k.as<int32_t>();
+    a.tiny_rows = p.tiny_rows.as<int32_t>();
+    a.tiny_k = p.tiny_k.as<int32_t>();
+    a.n_tiny = p.n_tiny;
     a.chunks = p.chunks.as<int4>();
     a.chunk_caps = p.chunk_caps.as<int4>();
     a.heavy = p.heavy.as<int4>();
@@ -765,6 +781,7 @@ int64_t handle_device_bytes(const ntc_handle* h) {
         b += (int64_t)(h->U[i].bytes + h->Ub[i].bytes + h->row_ptr[i].bytes + h->bucket[i].bytes + h->perm[i].bytes +
                        h->inv_dev[i].bytes + h->rows_dev[i].bytes);
         const ModePlan& p = h->plan[i];
+        b += (int64_t)(p.tiny_rows.bytes + p.tiny_k.bytes);
         b += (int64_t)(p.light_rows.bytes + p.light_k.bytes + p.chunks.bytes + p.chunk_caps.bytes + p.heavy.bytes +
                        p.bracket.bytes + p.heavy_cand.bytes + p.groups.bytes + p.heavy_groups.bytes);
     }
@@ -907,6 +924,8 @@ ntc_status ntc_set_param(ntc_handle* h, const char* key, double v) {
         if (!(v == 0.0 || v == 1.0 || v == 2.0 || v == 3.0))
             return fail(h, NTC_ERR_ARG, "gram_tc must be 0, 1, 2 or 3");
         h->gram_tc = (int)v;
+    } else if (k == "tiny_rows") {
+        h->tiny_rows = v != 0.0 ? 1 : 0;
     } else if (k == "test_gram_stall") {
         if (!(v >= 0 && v <= 1e9)) return fail(h, NTC_ERR_ARG, "test_gram_stall must be in [0, 1e9] cycles");
         h->test_stall_cycles = (long long)v;

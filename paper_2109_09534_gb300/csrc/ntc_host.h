@@ -50,10 +50,12 @@ struct ModePlan {
     int heavy_threshold = 0, chunk = 0;
     double bracket_z = 0.0;
     int64_t visits = 0, visits_heavy = 0, rows_updated = 0, rows_skipped = 0;
-    int n_light = 0, n_heavy = 0, n_chunks = 0;
+    int n_light = 0, n_heavy = 0, n_chunks = 0, n_tiny = 0;
+    bool tiny = false;   // rows of <= 509 observations went to the one-warp-per-row kernel
     int64_t cand_total = 0, extra_total = 0;
     int n_groups = 0;
     DevMem light_rows, light_k, chunks, chunk_caps, heavy, bracket, heavy_cand, groups, heavy_groups;
+    DevMem tiny_rows, tiny_k;
     DevMem vis_off;   // per chunk: start of its visit list in the epoch-permutation variant
 };
 
@@ -110,6 +112,7 @@ struct ntc_handle {
     ntc::DevMem partial, partial2, row_sum, stat, red, mask;
     int pipeline = 1;
     int gram_tc = 1;         // split-row Gram on the tensor cores where a kernel exists (R_pad 32, orders 2-4)
+    int tiny_rows = 1;       // rows of <= 509 observations one warp each (orders 2-4)
     // tensor-core Gram blocks that gave up a bounded wait, as last reported
     // to the caller; test hook that makes block 0 of each such launch give up
     unsigned long long faults_seen = 0;

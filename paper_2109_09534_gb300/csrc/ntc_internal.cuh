@@ -12,6 +12,9 @@ constexpr int kMaxOrder = 8;
 constexpr int kThreads = 256;        // threads per block of every row/chunk kernel
 constexpr int kLightMax = 4096;      // largest row whose keys fit in shared memory
 constexpr int kReduceGroup = 16;     // split-row partials summed per block of the group reduction
+// Largest row handled by one warp from sample to update (tiny_rows.cuh): its
+// positions, widened to whole Philox blocks, are at most 32 lanes x 16 keys.
+constexpr int kTinyMax = 509;
 
 // Bucket entry of one observation, seen from the mode being updated: the other
 // modes' indices in increasing mode order, then the value in the last word.
@@ -249,6 +252,10 @@ struct ModeArgs {
     // light rows
     const int32_t* light_rows;
     const int32_t* light_k;
+    // rows of at most 509 observations, one warp each (sample to update)
+    const int32_t* tiny_rows;
+    const int32_t* tiny_k;
+    int n_tiny;
     // heavy rows
     const int4* chunks;       // {heavy index, pos_begin, pos_end, cand_off}
     const int4* chunk_caps;   // {cand_cap, 0, 0, 0}

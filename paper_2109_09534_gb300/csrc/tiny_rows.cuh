@@ -1,0 +1,208 @@
+// tiny_rows.cuh -- Algorithm 1 for rows with few observations (n_p <= 509),
+// one warp per row from the sample to the updated factor row: keys of the
+// row's positions in registers, the exact k_p-subset of the sampling rule by
+// bisection on the key with warp reductions, the Gram/data sums accumulated in
+// registers, then H, the gradient, L_p and the projected momentum step
+// (finish_row_warp) on the warp's own H in shared memory.  Rating-shaped
+// tensors have hundreds of thousands of such rows per mode (users or items
+// with a handful of ratings); a block per row with a 4096-bin histogram select
+// and a reduced-sum round trip through global memory cost them far more than
+// their few visits.
+#pragma once
+
+#include "nmc_kernels.cuh"
+
+namespace ntc {
+
+template <int RP>
+struct TinyShape {
+    static constexpr int WARPS = RP > 32 ? 4 : 8;
+    static constexpr int RPL = RP > 32 ? 2 : 1;      // H rows owned per lane (rank r = lane + 32 t)
+    static constexpr int ND = RP / 2 + 1;            // stored diagonals of each owned row
+    // per warp: H (RP x (RP+1); the visit list, 512 u16, lives there until H
+    // is written, so the area holds at least 256 floats), b, the power-method
+    // vector, and k of one visit
+    static constexpr int HA = RP * (RP + 1) > 256 ? RP * (RP + 1) : 256;
+    static constexpr int PERW = HA + 3 * RP;
+    static constexpr size_t bytes() { return (size_t)WARPS * PERW * 4; }
+};
+
+template <int RP, int EW, bool BF16, int NOR>
+__global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArgs a) {
+    using TS = TinyShape<RP>;
+    static_assert(EW == 4 && NOR >= 1 && NOR <= 3, "orders 2-4");
+    extern __shared__ __align__(16) float tiny_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* H = tiny_smem + warp * TS::PERW;
+    float* bvec = H + TS::HA;
+    float* vsh = bvec + RP;
+    float* ksh = vsh + RP;
+    uint16_t* vis = reinterpret_cast<uint16_t*>(H);
+    const int i = blockIdx.x * TS::WARPS + warp;
+    if (i >= a.n_tiny) return;   // the same in every lane of the warp
+    const int row = a.tiny_rows[i];
+    const int k = a.tiny_k[i];
+    const int64_t q0 = a.row_ptr[row];
+    const int n = (int)(a.row_ptr[row + 1] - q0);
+    const uint32_t uq0 = (uint32_t)q0;
+
+    // ---- Alg. 1 line 5: the k smallest (key, position) of the row's positions
+    int nsel = k;
+    if (a.perm) {
+        // epoch-permutation variant: the slot's stretch of the row's permutation
+        const PermGen pg(a.ss.k0, a.ss.k1, a.ss.mode, a.perm_epoch, (uint32_t)row, (uint32_t)n);
+        const uint32_t s0 = (uint32_t)((a.perm_slot * k) % n);   // stretch start; s0 + j < 2n
+        pg.map_range(s0, lane, (uint32_t)k, 32, [&](uint32_t j, uint32_t x) { vis[j] = (uint16_t)x; });
+    } else {
+        // lane L: positions a0 + 16 L + j, j < 16 (four Philox blocks), a0 = q0 rounded down to 4
+        const uint32_t a0 = uq0 & ~3u;
+        const uint32_t qb = a0 + 16u * (uint32_t)lane;
+        const KeyGen kg(a.ss);
+        uint32_t kv[16];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint4 w = kg.key4((qb >> 2) + b);
+            kv[4 * b] = w.x;
+            kv[4 * b + 1] = w.y;
+            kv[4 * b + 2] = w.z;
+            kv[4 * b + 3] = w.w;
+        }
+        unsigned valid = 0u;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) valid |= (unsigned)(qb + j >= uq0 && qb + j - uq0 < (uint32_t)n) << j;
+        unsigned sel = valid;
+        if (k < n) {
+            // T = the smallest key value with #(key <= T) >= k
+            uint32_t lo = 0u, hi = 0xFFFFFFFFu;
+            while (lo < hi) {
+                const uint32_t mid = lo + ((hi - lo) >> 1);
+                int c = 0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) c += ((valid >> j) & 1u) && kv[j] <= mid ? 1 : 0;
+                c = (int)__reduce_add_sync(0xffffffffu, (unsigned)c);
+                if (c >= k) hi = mid;
+                else lo = mid + 1u;
+            }
+            unsigned lt = 0u, eq = 0u;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const bool v = (valid >> j) & 1u;
+                lt |= (unsigned)(v && kv[j] < lo) << j;
+                eq |= (unsigned)(v && kv[j] == lo) << j;
+            }
+            // keys equal to T are taken in position order (lane, then j) until k
+            const int need = k - (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(lt));
+            const int ce = __popc(eq);
+            int incl = ce;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int take = need - (incl - ce);
+            unsigned keep = 0u;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (((eq >> j) & 1u) && take > 0) {
+                    keep |= 1u << j;
+                    --take;
+                }
+            sel = lt | keep;
+        }
+        // visit list in position order
+        const int cnt = __popc(sel);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int off = incl - cnt;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if ((sel >> j) & 1u) vis[off++] = (uint16_t)(qb + j - uq0);
+        nsel = __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    if (a.mask_out) {
+        for (int v = lane; v < nsel; v += 32) a.mask_out[q0 + vis[v]] = 1;
+        return;
+    }
+
+    // ---- Gram / data sums (Alg. 1 lines 6, 7, 9): lane owns H rows r = lane + 32 t
+    // and keeps H[r][(r + d) mod RP] for d = 0 .. RP/2 (each unordered pair once,
+    // the pairs at distance RP/2 twice with identical sums)
+    float acc[TS::RPL][TS::ND];
+    float bacc[TS::RPL];
+#pragma unroll
+    for (int t = 0; t < TS::RPL; ++t) {
+        bacc[t] = 0.f;
+#pragma unroll
+        for (int d = 0; d < TS::ND; ++d) acc[t][d] = 0.f;
+    }
+    const Entry<EW>* bucket = reinterpret_cast<const Entry<EW>*>(a.bucket);
+    auto elem = [&](int o, int idx, int r) -> float {
+        if constexpr (BF16) {
+            const uint16_t u = static_cast<const uint16_t*>(a.other[o])[(size_t)idx * RP + r];
+            return __uint_as_float((uint32_t)u << 16);
+        } else {
+            return static_cast<const float*>(a.other[o])[(size_t)idx * RP + r];
+        }
+    };
+    for (int vb = 0; vb < nsel; vb += 32) {
+        const int nb = min(32, nsel - vb);
+        uint4 e = make_uint4(0u, 0u, 0u, 0u);   // lane v: the entry of visit vb + v
+        if (lane < nb) e = __ldg(reinterpret_cast<const uint4*>(bucket + q0 + vis[vb + lane]));
+        for (int v = 0; v < nb; ++v) {
+            const int i0 = (int)__shfl_sync(0xffffffffu, e.x, v);
+            const int i1 = NOR > 1 ? (int)__shfl_sync(0xffffffffu, e.y, v) : 0;
+            const int i2 = NOR > 2 ? (int)__shfl_sync(0xffffffffu, e.z, v) : 0;
+            const float x = __uint_as_float(__shfl_sync(0xffffffffu, e.w, v));
+            float kk[TS::RPL];
+#pragma unroll
+            for (int t = 0; t < TS::RPL; ++t) {
+                const int r = lane + 32 * t;
+                float p = 0.f;
+                if (r < RP) {
+                    p = elem(0, i0, r);
+                    if (NOR > 1) p *= elem(1, i1, r);
+                    if (NOR > 2) p *= elem(2, i2, r);
+                    ksh[r] = p;
+                }
+                kk[t] = p;
+                bacc[t] = fmaf(x, p, bacc[t]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < TS::RPL; ++t) {
+                const int r = lane + 32 * t;
+                if (r < RP) {
+#pragma unroll
+                    for (int d = 0; d < TS::ND; ++d) acc[t][d] = fmaf(kk[t], ksh[(r + d) & (RP - 1)], acc[t][d]);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // H = G + lambda I (line 9), full symmetric, stride RP + 1; b
+#pragma unroll
+    for (int t = 0; t < TS::RPL; ++t) {
+        const int r = lane + 32 * t;
+        if (r < RP) {
+#pragma unroll
+            for (int d = 0; d < TS::ND; ++d) {
+                const int c = (r + d) & (RP - 1);
+                H[r * (RP + 1) + c] = acc[t][d];
+                H[c * (RP + 1) + r] = acc[t][d];
+            }
+            bvec[r] = bacc[t];
+        }
+    }
+    __syncwarp();
+    for (int r = lane; r < a.rank; r += 32) H[r * (RP + 1) + r] += a.lambda;
+    __syncwarp();
+    // lines 8, 10-13
+    finish_row_warp<RP>(a, row, H, bvec, vsh, lane);
+}
+
+}  // namespace ntc

@@ -366,3 +366,52 @@ def test_pipelined_sampling_matches_stream_order(torch):
     with pytest.raises(ntc.NTCError) as e:
         g.set_param("pipeline", 0)
     assert e.value.status == ntc.NTC_ERR_STATE
+
+
+# ---- rows of at most 509 observations: one warp from sample to update ----
+
+def _tiny_problem(order, rank, seed):
+    """Rows of a few to a few hundred observations (Zipf skew), some above the
+    one-warp limit and some split, so that all three row paths meet in an epoch."""
+    dims = {2: [3000, 400], 3: [2000, 900, 300], 4: [900, 600, 200, 40]}[order]
+    return synth.make_problem(dims, rank, 150_000, index_dist="zipf", zipf_s=1.0, sigma=0.02,
+                              test_frac=0.05, seed=seed)
+
+
+@pytest.mark.parametrize("order,rank,extra", [
+    (3, 8, {}), (3, 16, {}), (3, 32, {}), (3, 64, {}), (3, 5, {}), (2, 24, {}), (4, 40, {}),
+    (3, 32, dict(storage_bf16=1)), (3, 20, dict(max_inner=3)), (3, 12, dict(power_warm=1, power_iters=3)),
+    (3, 32, dict(sampler=1))], ids=["r8", "r16", "r32", "r64", "r5", "o2r24", "o4r40", "bf16", "inner3",
+                                    "warm", "perm"])
+def test_tiny_rows_epoch(torch, order, rank, extra):
+    """Epoch parity with the one-warp kernel on, and the same epoch through the
+    block-per-row kernel (tiny_rows 0): both against the FP64 oracle, and the
+    sampled masks of both paths bit-exact."""
+    p = _tiny_problem(order, rank, seed=70 + rank + order)
+    oparams = {k: v for k, v in extra.items() if k in ("max_inner", "power_warm", "power_iters", "sampler")}
+    tol = (2e-2, 5e-2) if extra.get("storage_bf16") else (1e-5, 1e-4)
+    for tiny in (1, 0):
+        g, o = pair(p, torch, gparams=dict(extra, tiny_rows=tiny, heavy_rows=1024, chunk=2048), oparams=oparams)
+        g.epoch(0.2, seed=11)
+        o.epoch(0.2, seed=11)
+        for m in range(order):
+            assert_factor_close(g.get_factor(m), o.get_factor(m), *tol, f"tiny={tiny} mode {m}")
+        if not extra:
+            for m in range(order):
+                got = g.sample_mask(m, 0.2, 13, 3, 0, p.nnz)
+                np.testing.assert_array_equal(got, oracle_mask(p.idx_train, m, p.dims[m], 0.2, 13, 3, 0))
+        g.close()
+
+
+def test_tiny_rows_ties_and_full_rows(torch):
+    """c = 1 (every position of every row) and c = 0.999 (k = n - 1 for rows
+    below 1000 observations): the bisection selects all but the largest key."""
+    p = _tiny_problem(3, 16, seed=5)
+    for c in (1.0, 0.999, 0.5):
+        g, o = pair(p, torch, gparams=dict(heavy_rows=1024, chunk=2048))
+        g.snmc(1, c, seed=3)
+        o.snmc(1, c, seed=3)
+        assert_factor_close(g.get_factor(1), o.get_factor(1), 1e-6, 1e-5, f"c={c}")
+        got = g.sample_mask(2, c, 7, 1, 0, p.nnz)
+        np.testing.assert_array_equal(got, oracle_mask(p.idx_train, 2, p.dims[2], c, 7, 1, 0))
+        g.close()
