@@ -414,9 +414,15 @@ def run_ntc(args):
     bytes_per_launch = d["alg_bytes"] / max(d["launches"], 1)
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
     R, N = p.rank, p.order
-    # the tensor-core Gram runs at padded rank 32 (16 < R <= 32) and orders 2-4
-    tensor_gram = bool(args.gram_tc) and 16 < R <= 32 and N <= 4
-    gram_name = ("k_heavy_gram_tma" if args.gram_tc in (2, 3) else "k_heavy_gram_tc") if tensor_gram else "k_heavy_gram"
+    # the tensor-core Gram runs at padded ranks 32 (16 < R <= 32) and 64 (R > 32), orders 2-4
+    rp = 8 if R <= 8 else 16 if R <= 16 else 32 if R <= 32 else 64
+    tensor_gram = bool(args.gram_tc) and rp >= 32 and N <= 4
+    if not tensor_gram:
+        gram_name = "k_heavy_gram"
+    elif rp == 64:
+        gram_name = "k_heavy_gram_tc64"
+    else:
+        gram_name = "k_heavy_gram_tma" if args.gram_tc in (2, 3) else "k_heavy_gram_tc"
     kname = {"light": "k_light", "heavy_sample": "k_heavy_sample", "heavy_resolve": "k_heavy_resolve",
              "heavy_gram": gram_name, "finish": "k_rows_finish"}[dom]
     total_k = sum(v["ms"] for v in prof.values())
@@ -426,8 +432,8 @@ def run_ntc(args):
     gram_s = prof["heavy_gram"]["ms"] * 1e-3
     gram_tf = gram_visits * flops_per_visit / gram_s / 1e12 if gram_s > 0 else 0.0
     if tensor_gram:
-        # issued tensor work: one M=128 x N=32 x K=8 TF32 MMA per 8 visits
-        tc_flops_per_visit = 2 * 128 * 32
+        # issued tensor work: one M=128 x N=R_pad x K=8 TF32 MMA per 8 visits
+        tc_flops_per_visit = 2 * 128 * rp
         tc_tf = gram_visits * tc_flops_per_visit / gram_s / 1e12 if gram_s > 0 else 0.0
         tpk, tpk_kind = tf32_peak()
         compute_roof = {"roofline_tensor": {

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "gram_tc.cuh"
+#include "gram_tc64.cuh"
 #include "gram_tma.cuh"
 #include "nmc_kernels.cuh"
 #include "ntc_host.h"
@@ -17,6 +18,9 @@ namespace ntc {
 // the handle's "gram_tc" is 0; visits per staged tile:
 template <int RP, int EW, int NOR>
 constexpr bool kTensorGram = RP == 32 && EW == 4 && NOR > 0;
+// and at padded rank 64 (gram_tc64.cuh: M = 128 = 2 R, N = 64)
+template <int RP, int EW, int NOR>
+constexpr bool kTensorGram64 = RP == 64 && EW == 4 && NOR > 0;
 constexpr int kTcTile = 64;
 constexpr int kTcWindow = 1;   // tiles per tensor-memory accumulation window
 constexpr int kTcThreads = 128;
@@ -44,6 +48,8 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         if (e == cudaSuccess) e = set_smem(k_rows_finish<RP>, RowFinish<RP>::bytes());
         if constexpr (EW == 4 && NOR > 0)
             if (e == cudaSuccess) e = set_smem(k_tiny_rows<RP, EW, BF, NOR>, TinyShape<RP>::bytes());
+        if constexpr (kTensorGram64<RP, EW, NOR>)
+            if (e == cudaSuccess) e = set_smem(k_heavy_gram_tc64<EW, BF, NOR, kTcTile>, GramTC64<EW, kTcTile>::BYTES);
         if constexpr (kTensorGram<RP, EW, NOR>) {
             if (e == cudaSuccess) e = set_smem(k_heavy_gram_tc<EW, BF, NOR, kTcTile, kTcWindow, kTcThreads>, GramTC<EW, kTcTile, kTcWindow, kTcThreads>::BYTES);
             if (e == cudaSuccess)
@@ -152,6 +158,13 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
                     } else if (h->gram_tc) {
                         using T = GramTC<EW, kTcTile, kTcWindow, kTcThreads>;
                         k_heavy_gram_tc<EW, BF, NOR, kTcTile, kTcWindow, kTcThreads><<<p.n_chunks + p.n_heavy, T::NT, T::BYTES, s>>>(a);
+                        tensor = true;
+                    }
+                }
+                if constexpr (kTensorGram64<RP, EW, NOR>) {
+                    if (h->gram_tc) {
+                        using T = GramTC64<EW, kTcTile>;
+                        k_heavy_gram_tc64<EW, BF, NOR, kTcTile><<<p.n_chunks + p.n_heavy, T::NT, T::BYTES, s>>>(a);
                         tensor = true;
                     }
                 }

@@ -126,3 +126,57 @@ def test_wait_timeout_is_reported_and_the_handle_recovers(torch, gram_tc):
         o2.snmc(m, 0.1, seed=9)
         assert_factor_close(g2.get_factor(m), o2.get_factor(m), 1e-6, 1e-5, str(m))
     assert g2.stats()["wait_timeouts"] == 0
+
+
+# ---- padded rank 64: M = 128 = 2 R, N = 64 (gram_tc64.cuh) ----
+
+CASES64 = {
+    "zipf2k_r64": lambda: small_zipf(rank=64, nnz=150_000),
+    "zipf2k_r40": lambda: small_zipf(rank=40, nnz=150_000),
+    "order2_r64": lambda: synth.make_problem([400, 250], 64, 60_000, index_dist="zipf", sigma=0.01,
+                                             test_frac=0.05, seed=23),
+    "order4_r50": lambda: synth.make_problem([120, 90, 40, 30], 50, 100_000, index_dist="zipf", sigma=0.01,
+                                             test_frac=0.05, seed=24),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES64))
+@pytest.mark.parametrize("split", list(SPLITS))
+def test_single_update_tensor_gram_rank64(torch, case, split):
+    """Padded rank 64: tensor-core Gram vs FP64 within 1e-6 after one mode
+    update, and vs the FP32 FMA Gram of the same handle."""
+    p = CASES64[case]()
+    got, st = one_update(p, torch, 1, split)
+    assert st["visits_heavy"] > 0 and st["wait_timeouts"] == 0
+    fma, _ = one_update(p, torch, 0, split)
+    for m, (a, want) in enumerate(got):
+        assert_factor_close(a, want, 1e-6, 1e-5, str((case, split, m)))
+        assert_factor_close(a, fma[m][0], 1e-6, 1e-5, str((case, split, m, "fma")))
+
+
+def test_tensor_gram_rank64_bf16_and_epoch(torch):
+    p = CASES64["zipf2k_r64"]()
+    tc, st = one_update(p, torch, 1, "small", bf16=True)
+    fma, _ = one_update(p, torch, 0, "small", bf16=True)
+    assert st["wait_timeouts"] == 0
+    for m in range(p.order):
+        assert rel_err(tc[m][0], tc[m][1]) <= 2e-2, m
+        assert_factor_close(tc[m][0], fma[m][0], 1e-6, 1e-5, str(m))
+    g, o = pair(p, torch, gparams=dict(heavy_rows=128, gram_tc=1))
+    g.epoch(0.1, seed=5)
+    o.epoch(0.1, seed=5)
+    for m in range(3):
+        assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, str(m))
+    assert g.stats()["wait_timeouts"] == 0
+
+
+def test_wait_timeout_rank64(torch):
+    from paper_2109_09534_gb300 import ntc
+    p = CASES64["zipf2k_r40"]()
+    g, _ = pair(p, torch, gparams=dict(heavy_rows=128, chunk=700, test_gram_stall=20000))
+    g.snmc(0, 0.1, seed=3)
+    assert g.stats()["wait_timeouts"] == 1
+    with pytest.raises(ntc.NTCError) as e:
+        g.sync()
+    assert e.value.status == ntc.NTC_ERR_CUDA
+    g.close()
