@@ -431,21 +431,23 @@ def run_ntc(args):
     gram_visits = prof["heavy_gram"]["alg_bytes"] // ((N - 1) * 4 + 4 + (N - 1) * R * s_bytes)
     gram_s = prof["heavy_gram"]["ms"] * 1e-3
     gram_tf = gram_visits * flops_per_visit / gram_s / 1e12 if gram_s > 0 else 0.0
+    # the split-row Gram's algorithmic flops against the FP32 FMA peak (the
+    # ALU roofline of the method's arithmetic, whichever unit runs it) and,
+    # on the tensor cores, its issued TF32 work against the tensor peak
+    compute_roof = {"roofline_alu": {
+        "kernel": gram_name, "achieved": gram_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+        "frac": gram_tf / fp32_peak if fp32_peak else None,
+        "peak_kind": "measured FP32 FMA microbenchmark, same run", "flops_per_visit": flops_per_visit}}
     if tensor_gram:
         # issued tensor work: one M=128 x N=R_pad x K=8 TF32 MMA per 8 visits
         tc_flops_per_visit = 2 * 128 * rp
         tc_tf = gram_visits * tc_flops_per_visit / gram_s / 1e12 if gram_s > 0 else 0.0
         tpk, tpk_kind = tf32_peak()
-        compute_roof = {"roofline_tensor": {
+        compute_roof["roofline_tensor"] = {
             "kernel": gram_name, "achieved": tc_tf, "peak": tpk, "unit": "TFLOP/s", "frac": tc_tf / tpk,
             "peak_kind": tpk_kind, "dtype": "tf32 (3xTF32 split of FP32)",
             "flops_per_visit_issued": tc_flops_per_visit, "alg_flops_per_visit": flops_per_visit,
-            "alg_tflops": gram_tf}}
-    else:
-        compute_roof = {"roofline_alu": {
-            "kernel": gram_name, "achieved": gram_tf, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": gram_tf / fp32_peak if fp32_peak else None,
-            "peak_kind": "measured FP32 FMA microbenchmark, same run", "flops_per_visit": flops_per_visit}}
+            "alg_tflops": gram_tf}
 
     # end to end through the C ABI with pinned host buffers
     idx_pin = torch.from_numpy(np.ascontiguousarray(p.idx_train)).pin_memory()
