@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--serve-nnz", default="1000000,5000000", help="log-uniform observation range")
     ap.add_argument("--serve-budget", type=float, default=150e9, help="HBM budget, bytes")
     ap.add_argument("--serve-max-epochs", type=int, default=40)
+    ap.add_argument("--serve-gen", default="host", choices=["host", "device"],
+                    help="draw the jobs' data on the host up front, or on the GPU one by one as they arrive "
+                         "(always device with --serve-full)")
     ap.add_argument("--serve-qps", type=float, default=10000.0, help="prediction queries per second")
     # convergence study (synthetic twin of the MovieLens experiments)
     ap.add_argument("--study", default="", choices=["", "convergence"])
@@ -541,8 +544,25 @@ def run_serve(args):
                                  nnz_range=(nlo, nhi))
     sigma = 0.01
     target = 1.1 * sigma
+    device_gen = args.serve_full or args.serve_gen == "device"
     t_gen = time.perf_counter()
-    probs = [synth.serving_job(s, sigma=sigma, test_frac=0.01) for s in specs]
+    probs = None
+    jobq = None
+    if device_gen:
+        # jobs drawn on the GPU one by one, in arrival order and a few ahead of
+        # the submission loop; a job's host arrays are released once admitted
+        import queue
+        import threading
+        jobq = queue.Queue(maxsize=6)
+
+        def produce():
+            torch.cuda.set_device(0)
+            for s in specs:
+                jobq.put((s, synth.serving_job_device(s, sigma=sigma, test_frac=0.01)))
+        gen_thread = threading.Thread(target=produce, daemon=True)
+        gen_thread.start()
+    else:
+        probs = [synth.serving_job(s, sigma=sigma, test_frac=0.01) for s in specs]
     t_gen = time.perf_counter() - t_gen
     srv = ntc.Server(args.serve_budget, 64)
     srv.set_param("max_enqueue_per_step", 2)
@@ -550,20 +570,34 @@ def run_serve(args):
     clocks.start()
     t0 = srv.now()
     ids = []
-    for k, (s, p) in enumerate(zip(specs, probs)):
-        ids.append(srv.submit(p.dims, p.rank, p.lam, p.c, p.idx_train, p.val_train, p.idx_test, p.val_test,
-                              target, args.serve_max_epochs, arrival=t0 + s.arrival, seed=1000 + 97 * k,
-                              init_seed=3, storage_bf16=s.storage_bf16))
+    dims_of = {}           # job id -> mode sizes (queries)
+    obs_ratio = []         # observations per factor entry, per job
+
+    def submit_job(k, s, p):
+        jid = srv.submit(p.dims, p.rank, p.lam, p.c, p.idx_train, p.val_train, p.idx_test, p.val_test,
+                         target, args.serve_max_epochs, arrival=t0 + s.arrival, seed=1000 + 97 * k,
+                         init_seed=3, storage_bf16=s.storage_bf16)
+        ids.append(jid)
+        dims_of[jid] = list(p.dims)
+        obs_ratio.append(p.nnz / float(p.rank * sum(p.dims)))
+
+    if not device_gen:
+        for k, (s, p) in enumerate(zip(specs, probs)):
+            submit_job(k, s, p)
     rng = np.random.default_rng(7)
     lat = []
     t_q = srv.now()
     pending = []          # arrival times of queries not yet served
     while True:
+        while device_gen and len(ids) < len(specs) and not jobq.empty():
+            s, p = jobq.get()
+            submit_job(len(ids), s, p)
+            del p
         srv.step()
         now = srv.now()
         # queries that arrived since the last tick (Poisson), against running
         # jobs: while none is running there is nothing to query
-        running = [(j, probs[j]) for j in ids if srv.job_info(j)["state"] == ntc.JOB_RUNNING]
+        running = [(j, dims_of[j]) for j in ids if srv.job_info(j)["state"] == ntc.JOB_RUNNING]
         if running:
             nq = rng.poisson(args.serve_qps * (now - t_q))
             pending += list(np.sort(rng.uniform(t_q, now, nq)))
@@ -572,14 +606,14 @@ def run_serve(args):
             pick = rng.integers(0, len(running), len(pending))
             q_job = np.array([j for j, _ in running], dtype=np.int64)[pick]
             dmat = np.ones((len(running), 8))
-            for r, (_, p) in enumerate(running):
-                dmat[r, :len(p.dims)] = p.dims
+            for r, (_, dm) in enumerate(running):
+                dmat[r, :len(dm)] = dm
             q_idx = (rng.random((len(pending), 8)) * dmat[pick]).astype(np.int32)   # padding columns stay 0
             srv.predict(q_job, q_idx)
             t_ret = srv.now()
             lat += [t_ret - a for a in pending]
             pending = []
-        if all(srv.job_info(j)["state"] >= ntc.JOB_DONE for j in ids):
+        if len(ids) == len(specs) and all(srv.job_info(j)["state"] >= ntc.JOB_DONE for j in ids):
             break
         time.sleep(0.0002)
     wall = srv.now() - t0
@@ -599,9 +633,14 @@ def run_serve(args):
             "entries_per_s": st["entries"] / wall, "epochs": st["epochs"], "wall_s": wall,
             "peak_running": st["peak_running"], "peak_bytes": st["peak_bytes"], "budget_bytes": args.serve_budget,
             "job_results": [{"order": len(s.dims), "rank": s.rank, "nnz": s.nnz, "bf16": s.storage_bf16,
+                             "obs_per_param": round(r, 2),
                              "epochs": i["epochs"], "rmse0": round(i["rmse0"], 5), "rmse": round(i["rmse"], 5),
                              "reached": i["reached"], "queue_s": round(i["t_admit"] - i["t_arrival"], 4),
-                             "run_s": round(i["t_done"] - i["t_admit"], 4)} for s, i in zip(specs, infos)],
+                             "run_s": round(i["t_done"] - i["t_admit"], 4)}
+                            for s, i, r in zip(specs, infos, obs_ratio)],
+            "rmse_over_sigma": {q: float(np.percentile([i["rmse"] / sigma for i in infos], q))
+                                for q in (10, 50, 90)},
+            "generation": "device (torch, per job, a few ahead of submission)" if device_gen else "host (numpy)",
             "n_gpus": 1, "data": "synthetic", "dtype": "f32 / bf16-storage (half the jobs each)", "clocks": clk,
             "config": {"workload": f"{args.serve_jobs} jobs, Poisson {args.serve_rate}/s, order 3-4, mode sizes "
                                    f"log-uniform {args.serve_dims}, R in 8/16/32/64, observations log-uniform "

@@ -236,6 +236,44 @@ def serving_job(spec: JobSpec, sigma: float = 0.01, test_frac: float = 0.01) -> 
                         name=f"job-{len(spec.dims)}way-R{spec.rank}-{spec.nnz}")
 
 
+def serving_job_device(spec: JobSpec, sigma: float = 0.01, test_frac: float = 0.01, device: str = "cuda",
+                       chunk: int = 1 << 22) -> Problem:
+    """The job of serving_job's recipe (planted U[0,1] factors of the spec's
+    rank, uniform indices, Gaussian noise sigma, lambda = 1e-3, c = 0.1) drawn
+    with torch's generator on `device`, for streams whose jobs are too large to
+    draw on the host in time: seeded by the spec (the same job on the same
+    device and torch version), not the same draws as serving_job.  Planted
+    values are float32 products summed in float64, as in planted_values.  The
+    arrays are returned on the host; the planted factors are not kept."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(spec.data_seed))
+    dims, R, n = [int(d) for d in spec.dims], int(spec.rank), int(spec.nnz)
+    F = [torch.rand(d, R, generator=g, device=device, dtype=torch.float32) for d in dims]
+    idx = torch.empty(n, len(dims), dtype=torch.int32, device=device)
+    for i, d in enumerate(dims):
+        idx[:, i] = torch.randint(0, d, (n,), generator=g, device=device, dtype=torch.int32)
+    vals = torch.empty(n, dtype=torch.float32, device=device)
+    clean = torch.empty(n, dtype=torch.float64, device=device)
+    for s0 in range(0, n, chunk):
+        s1 = min(n, s0 + chunk)
+        ix = idx[s0:s1].long()
+        prod = F[0].index_select(0, ix[:, 0])
+        for i in range(1, len(dims)):
+            prod.mul_(F[i].index_select(0, ix[:, i]))
+        c = prod.sum(dim=1, dtype=torch.float64)
+        clean[s0:s1] = c
+        noise = torch.randn(s1 - s0, generator=g, device=device, dtype=torch.float64)
+        vals[s0:s1] = (c + sigma * noise).to(torch.float32)
+    n_test = int(round(test_frac * n))
+    n_train = n - n_test
+    idx_h, vals_h, clean_h = idx.cpu().numpy(), vals.cpu().numpy(), clean.cpu().numpy()
+    return Problem(dims=dims, rank=R, lam=1e-3, c=0.1, factors=[], idx_train=idx_h[:n_train],
+                   val_train=vals_h[:n_train], idx_test=np.ascontiguousarray(idx_h[n_train:]),
+                   val_test=vals_h[n_train:], val_test_clean=clean_h[n_train:], sigma=sigma,
+                   name=f"job-{len(dims)}way-R{R}-{n}-device")
+
+
 def uber_twin(seed: int = 1) -> Problem:
     """Uber-Pickups-shaped timing twin (Sec. IV-C): 183 x 24 x 1140 x 1717,
     3,309,490 uniform draws of a planted rank-10 tensor with U[0,1] factors,
