@@ -87,7 +87,7 @@ def parse():
                          "(always device with --serve-full)")
     ap.add_argument("--serve-qps", type=float, default=10000.0, help="prediction queries per second")
     # convergence study (synthetic twin of the MovieLens experiments)
-    ap.add_argument("--study", default="", choices=["", "convergence"])
+    ap.add_argument("--study", default="", choices=["", "convergence", "packing"])
     ap.add_argument("--study-trials", type=int, default=5)
     ap.add_argument("--study-epochs", type=int, default=100)
     ap.add_argument("--study-nnz", type=int, default=10_000_000)
@@ -705,8 +705,85 @@ def run_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_packing_study(args):
+    """Does the server leave throughput on the table by running each job's
+    epochs as its own launches on its own stream instead of packing several
+    jobs' updates into shared launches?  The same work three ways: J jobs of n
+    observations at once through the server, the same J jobs one at a time,
+    and one handle holding all J n observations (the throughput a perfectly
+    packed launch sequence could approach).  Each job runs E epochs."""
+    import numpy as np
+    import torch
+
+    from paper_2109_09534_gb300 import ntc, synth
+
+    torch.cuda.set_device(0)
+    J, n, E, R, dims = 16, 2_000_000, 10, 16, [20_000, 20_000, 20_000]
+    specs = [synth.JobSpec(0.0, dims, R, n, 0, 900 + k) for k in range(J)]
+    probs = [synth.serving_job_device(s, sigma=0.01, test_frac=0.01) for s in specs]
+    res = {}
+    for mode, max_running in (("concurrent", J), ("one_at_a_time", 1)):
+        srv = ntc.Server(150e9, max_running)
+        srv.set_param("max_enqueue_per_step", 4)
+        ids = [srv.submit(p.dims, p.rank, p.lam, p.c, p.idx_train, p.val_train, p.idx_test, p.val_test, 0.0, E,
+                          arrival=0.0, seed=10 * k, init_seed=3) for k, p in enumerate(probs)]
+        # admission (upload and bucketing) is not part of the comparison: time
+        # from the first epoch enqueued to the last collected
+        while any(srv.job_info(j)["state"] == ntc.JOB_QUEUED for j in ids[:max_running]):
+            srv.step()
+            time.sleep(0.0005)
+        t0 = time.perf_counter()
+        while not all(srv.job_info(j)["state"] >= ntc.JOB_DONE for j in ids):
+            srv.step()
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        res[mode] = {"wall_s": wall, "entries_per_s": st["entries"] / wall, "epochs": st["epochs"],
+                     "peak_running": st["peak_running"]}
+        srv.close()
+    # one handle with all J n observations and J times the rows per mode, so that
+    # its rows hold as many observations as each job's: the same kernels on a
+    # J-times larger grid, which is what packed launches of the J jobs would run
+    big = synth.serving_job_device(synth.JobSpec(0.0, [J * d for d in dims], R, J * n, 0, 950), sigma=0.01,
+                                   test_frac=0.01)
+    s = torch.cuda.current_stream()
+    g = ntc.NTC(big.dims, big.rank, big.lam, stream=s.cuda_stream)
+    g.set_observed(big.idx_train, big.val_train)
+    g.epoch(big.c, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for e in range(E):
+        g.epoch(big.c, seed=2 + e)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    res["one_handle_all_observations"] = {"wall_s": wall, "entries_per_s": big.nnz * E / wall,
+                                          "dims": big.dims, "launches_per_epoch": g.stats()["kernel_launches"]}
+    # one job alone
+    g1 = ntc.NTC(probs[0].dims, R, probs[0].lam, stream=s.cuda_stream)
+    g1.set_observed(probs[0].idx_train, probs[0].val_train)
+    g1.epoch(0.1, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for e in range(E):
+        g1.epoch(0.1, seed=2 + e)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    res["one_job_alone"] = {"wall_s": wall, "entries_per_s": probs[0].nnz * E / wall,
+                            "launches_per_epoch": g1.stats()["kernel_launches"]}
+    line = {"metric": "serving packing study: aggregate observed entries/s", "mode": "study", "unit": "entries/s",
+            "data": "synthetic", "config": {"workload": f"{J} jobs of {n} uniform observations, dims {dims}, "
+                                                         f"R={R}, FP32, c=0.1, {E} epochs each"},
+            "results": res,
+            "concurrent_over_one_handle": res["concurrent"]["entries_per_s"] /
+            res["one_handle_all_observations"]["entries_per_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.study == "packing":
+        run_packing_study(args)
+        return
     if args.study:
         run_study(args)
         return
