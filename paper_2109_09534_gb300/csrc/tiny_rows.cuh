@@ -1,7 +1,8 @@
 // tiny_rows.cuh -- Algorithm 1 for rows with few observations (n_p <= 509),
 // one warp per row from the sample to the updated factor row: keys of the
-// row's positions in registers, the exact k_p-subset of the sampling rule by
-// bisection on the key with warp reductions, the Gram/data sums accumulated in
+// row's positions in registers, the exact k_p-subset of the sampling rule by a
+// byte-wise radix select of the k_p-th key (a 256-bin warp histogram per
+// byte), ties taken in position order, the Gram/data sums accumulated in
 // registers, then H, the gradient, L_p and the projected momentum step
 // (finish_row_warp) on the warp's own H in shared memory.  Rating-shaped
 // tensors have hundreds of thousands of such rows per mode (users or items
@@ -21,9 +22,9 @@ struct TinyShape {
     static constexpr int ND = RP / 2 + 1;            // stored diagonals of each owned row
     // per warp: H (RP x (RP+1); the visit list, 512 u16, lives there until H
     // is written, so the area holds at least 256 floats), b, the power-method
-    // vector, and k of one visit
+    // vector, k of one visit, and the select's 256-bin histogram
     static constexpr int HA = RP * (RP + 1) > 256 ? RP * (RP + 1) : 256;
-    static constexpr int PERW = HA + 3 * RP;
+    static constexpr int PERW = HA + 3 * RP + 256;
     static constexpr size_t bytes() { return (size_t)WARPS * PERW * 4; }
 };
 
@@ -37,6 +38,7 @@ __global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArg
     float* bvec = H + TS::HA;
     float* vsh = bvec + RP;
     float* ksh = vsh + RP;
+    unsigned* hist = reinterpret_cast<unsigned*>(ksh + RP);
     uint16_t* vis = reinterpret_cast<uint16_t*>(H);
     const int i = blockIdx.x * TS::WARPS + warp;
     if (i >= a.n_tiny) return;   // the same in every lane of the warp
@@ -72,17 +74,51 @@ __global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArg
         for (int j = 0; j < 16; ++j) valid |= (unsigned)(qb + j >= uq0 && qb + j - uq0 < (uint32_t)n) << j;
         unsigned sel = valid;
         if (k < n) {
-            // T = the smallest key value with #(key <= T) >= k
-            uint32_t lo = 0u, hi = 0xFFFFFFFFu;
-            while (lo < hi) {
-                const uint32_t mid = lo + ((hi - lo) >> 1);
-                int c = 0;
+            // T = the k-th smallest key (the smallest key value with #(key <= T)
+            // >= k), one byte per pass from the top: a 256-bin histogram of the
+            // keys that match the digits found so far, and the bin where the
+            // running count reaches k
+            uint32_t prefix = 0u;
+            int rem = k;
+#pragma unroll 1
+            for (int shift = 24; shift >= 0; shift -= 8) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) c += ((valid >> j) & 1u) && kv[j] <= mid ? 1 : 0;
-                c = (int)__reduce_add_sync(0xffffffffu, (unsigned)c);
-                if (c >= k) hi = mid;
-                else lo = mid + 1u;
+                for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0u;
+                __syncwarp();
+                const uint32_t hmask = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (((valid >> j) & 1u) && (kv[j] & hmask) == (prefix & hmask))
+                        atomicAdd(&hist[(kv[j] >> shift) & 255u], 1u);
+                __syncwarp();
+                unsigned c[8], own = 0u;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    c[b] = hist[lane * 8 + b];
+                    own += c[b];
+                }
+                unsigned incl = own;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const unsigned excl = incl - own;
+                unsigned found = 0u;   // lane holding the bin: 1 + digit in bits 0-8, count below in 9-31
+                if (excl < (unsigned)rem && (unsigned)rem <= incl) {
+                    unsigned cum = excl;
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        if (!found && cum + c[b] >= (unsigned)rem) found = (1u + lane * 8 + b) | (cum << 9);
+                        cum += c[b];
+                    }
+                }
+                found = __reduce_or_sync(0xffffffffu, found);
+                prefix |= (((found & 511u) - 1u) & 255u) << shift;
+                rem -= (int)(found >> 9);
+                __syncwarp();
             }
+            const uint32_t lo = prefix;
             unsigned lt = 0u, eq = 0u;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
