@@ -175,7 +175,8 @@ def tf32_peak():
 
 # sources of the epoch kernels (the serving runtime and the host API are not
 # part of what the DRAM counters measured)
-KERNEL_SOURCES = ("ntc_internal.cuh", "nmc_kernels.cuh", "gram_tc.cuh", "gram_tma.cuh", "launch_rp.cuh",
+KERNEL_SOURCES = ("ntc_internal.cuh", "nmc_kernels.cuh", "gram_tc.cuh", "gram_tc64.cuh", "gram_tma.cuh",
+                  "tiny_rows.cuh", "launch_rp.cuh",
                   "nmc_rp8.cu", "nmc_rp16.cu", "nmc_rp32.cu", "nmc_rp64.cu")
 
 
