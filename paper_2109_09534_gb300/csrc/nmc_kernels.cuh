@@ -820,6 +820,14 @@ __global__ void __launch_bounds__(kLightThreads, 4) k_light(ModeArgs a) {
         gr.reduce(red, a.row_sum + (size_t)blockIdx.x * G::PW);
         return;
     }
+    // the row's bucket entries (contiguous, 16-byte aligned, a multiple of 16
+    // bytes) start toward L2 now, so that the Gram's sampled entry reads after
+    // the selection find them there
+    if (threadIdx.x == 0) {
+        const unsigned char* src = static_cast<const unsigned char*>(a.bucket) + (size_t)q0 * (EW * 4);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"((uint32_t)n * (EW * 4))
+                     : "memory");
+    }
     // Alg. 1 line 5: the k smallest (key, position) of the row's n positions
     unsigned long long T = ~0ull;
     if (k < n) {
@@ -924,7 +932,7 @@ constexpr int kResolvePer = 8;   // candidates per thread per round of the resol
 // same in every thread).  Rounds start at pb rounded down to a multiple of 4,
 // so that a thread's 16 positions are four whole Philox blocks.
 __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan_tmp) {
-    static_assert(kSamplePer % 4 == 0, "whole Philox blocks per thread");
+    static_assert(kSamplePer == 16, "whole Philox blocks per thread, 16-bit position masks");
     const int4 c = a.chunks[ch];
     const int h = c.x;
     const uint32_t pb = (uint32_t)c.y, pe = (uint32_t)c.z;
@@ -938,27 +946,40 @@ __device__ __forceinline__ int sample_chunk(const ModeArgs& a, int ch, int* scan
     int nsel = 0, ncand = 0;
     for (uint32_t base = pb & ~3u; base < pe; base += kThreads * kSamplePer) {
         const uint32_t q0 = base + threadIdx.x * kSamplePer;
-        // only the first and the last round of a chunk hold positions outside it
-        const bool edge = base < pb || base + kThreads * kSamplePer > pe;
-        uint32_t kv[kSamplePer];
-#pragma unroll
-        for (int b = 0; b < kSamplePer / 4; ++b) {
-            uint4 w = make_uint4(0u, 0u, 0u, 0u);
-            if (q0 + 4u * b < pe) w = kg.key4((q0 >> 2) + b);
-            kv[4 * b] = w.x;
-            kv[4 * b + 1] = w.y;
-            kv[4 * b + 2] = w.z;
-            kv[4 * b + 3] = w.w;
+        // bits of this thread's positions inside the chunk: only the first and
+        // the last round of a chunk hold positions outside it
+        unsigned vm = 0xFFFFu;
+        if (base < pb || base + kThreads * kSamplePer > pe) {
+            const unsigned jl = q0 >= pb ? 0u : min(pb - q0, 16u), jh = q0 >= pe ? 0u : min(pe - q0, 16u);
+            vm = jh > jl ? (((1u << jh) - 1u) & ~((1u << jl) - 1u)) : 0u;
         }
         // bit j of dm / cm: position q0 + j is certain / a candidate
+        uint32_t kv[kSamplePer];
         unsigned dm = 0u, cm = 0u;
+        if (lo_all) {
+            // k = n: every position, no keys
 #pragma unroll
-        for (int j = 0; j < kSamplePer; ++j) {
-            const bool in = !edge || (q0 + j >= pb && q0 + j < pe);
-            const bool d = in && (lo_all || kv[j] < lo);
-            const bool cn = in && !d && (hi_all || kv[j] < hi);
-            dm |= (unsigned)d << j;
-            cm |= (unsigned)cn << j;
+            for (int j = 0; j < kSamplePer; ++j) kv[j] = 0u;
+            dm = vm;
+        } else {
+#pragma unroll
+            for (int b = 0; b < kSamplePer / 4; ++b) {
+                uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                if (q0 + 4u * b < pe) w = kg.key4((q0 >> 2) + b);
+                kv[4 * b] = w.x;
+                kv[4 * b + 1] = w.y;
+                kv[4 * b + 2] = w.z;
+                kv[4 * b + 3] = w.w;
+            }
+            // one compare and one conditional bit set per key and bound
+#pragma unroll
+            for (int j = 0; j < kSamplePer; ++j) {
+                dm = kv[j] < lo ? dm | (1u << j) : dm;
+                cm = kv[j] < hi ? cm | (1u << j) : cm;
+            }
+            if (hi_all) cm = 0xFFFFu;
+            dm &= vm;
+            cm &= vm & ~dm;
         }
         int tot;
         const int packed = block_exclusive_scan(__popc(dm) | (__popc(cm) << 16), scan_tmp, &tot);

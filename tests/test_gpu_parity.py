@@ -29,6 +29,10 @@ CASES = {
 }
 # small thresholds so that even the small cases have split (heavy) rows and many chunks
 SPLIT = dict(heavy_rows=128, chunk=700)
+# every row of at most 4096 observations through the block-per-row kernel
+# (none through the warp-per-row one)
+LIGHT = dict(tiny_rows=0)
+LAYOUTS = {"default": {}, "split": SPLIT, "light": LIGHT}
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -46,8 +50,8 @@ def test_bucket_bit_exact(torch, case):
 @pytest.mark.parametrize("case", ["cube100", "zipf2k", "uni4way", "order5"])
 @pytest.mark.parametrize("c", [0.1, 0.37, 1.0])
 @pytest.mark.parametrize("params", [{}, SPLIT, dict(SPLIT, bracket_z=0.0), dict(SPLIT, bracket_z=2.0),
-                                    dict(SPLIT, bracket_z=1e5)], ids=["default", "split", "fallback",
-                                                                     "narrow", "wide"])
+                                    dict(SPLIT, bracket_z=1e5), LIGHT],
+                         ids=["default", "split", "fallback", "narrow", "wide", "light"])
 def test_sampler_bit_exact(torch, case, c, params):
     p = CASES[case]()
     g = ntc.NTC(p.dims, p.rank, p.lam, stream=torch.cuda.current_stream().cuda_stream, **params)
@@ -83,11 +87,11 @@ def test_fallback_selector_is_counted(torch):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("split", [False, True])
-def test_single_mode_update(torch, case, split):
+@pytest.mark.parametrize("layout", list(LAYOUTS))
+def test_single_mode_update(torch, case, layout):
     """One call of Algorithm 1 from identical factors: FP32 vs FP64 within 1e-6."""
     p = CASES[case]()
-    g, o = pair(p, torch, gparams=SPLIT if split else {})
+    g, o = pair(p, torch, gparams=LAYOUTS[layout])
     for m in range(p.order):
         g.ao_iter = 3
         o.ao_iter = 3
