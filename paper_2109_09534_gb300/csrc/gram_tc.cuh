@@ -9,14 +9,15 @@
 // small = k - big (exact in FP32; read as TF32 by the tensor core, an error of
 // at most 2^-21 |k| of either sign).  Per tile of VT visits the block stages
 // S = [big; small] (2R rows x VT visits) in shared memory, and one MMA per 8
-// visits accumulates D = S big^T in tensor memory: rows 0..R-1 give
-// bb = sum big big^T, rows R..2R-1 give sb = sum small big^T, and
+// visits (M = 64 = 2R, N = R) accumulates D = S big^T in tensor memory: rows
+// 0..R-1 give bb = sum big big^T, rows R..2R-1 give sb = sum small big^T, and
 // G = bb + sb + sb^T (the dropped small small^T is about 2^-24 of G).
 // The tensor core's FP32 accumulation is biased (measured: accumulating a
 // whole chunk in tensor memory moved G by up to 3e-5 relative), so D restarts
-// every tile (VT/8 MMAs) and a warp pair adds each finished tile into FP32
-// registers: even tiles' rows sit in TMEM lanes 0-63 (bb row i in lane i of
-// warp 0, sb row i in warp 1), odd tiles' in lanes 64-127 (warps 2 and 3).
+// every tile (VT/8 MMAs) and every warp adds its slice of each finished tile
+// into FP32 registers: with M = 64, D row r sits in TMEM lane 32 (r / 16) +
+// r % 16, so warp w holds rows 16 w .. 16 w + 15 in its lanes 0-15, and the
+// 16x32bx2 load shape hands its 32 threads one row and 16 columns each.
 // b = sum x_e k_e stays on the FP32 FMA path.
 #pragma once
 
@@ -146,14 +147,16 @@ __device__ __forceinline__ float round_tf32(float x) {
 
 // Block shape and shared-memory map of the tensor-core Gram.  FW = tiles per
 // tensor-memory accumulation window (D restarts, and is folded into the
-// registers, every FW tiles); only 1 is valid with the alternating lane
-// placement below, since an even and an odd tile would add their rows onto
-// each other's ignored rows within one window.
+// registers, every FW tiles); only 1 is valid.  k_heavy_gram_tc issues M = 64
+// MMAs (IDESC64); the M = 128 form with the alternating lane placement
+// described below (IDESC, odd tiles' A started 8 row groups early) is the one
+// the TMA-gather kernel (gram_tma.cuh) uses, and the shared-memory reach below
+// covers it.
 template <int EW, int VT, int FW, int NT_>
 struct GramTC {
     static constexpr int RP = 32;
     static constexpr int NT = NT_;                // threads: 128 or 256
-    static constexpr int BLOCKS = NT == 128 ? 4 : 3;   // resident blocks per SM (registers)
+    static constexpr int BLOCKS = NT == 128 ? 4 : 3;   // resident blocks per SM
     // D's 2R useful rows sit in TMEM lanes 0..63 for even tiles and, with A's
     // descriptor started 8 row groups early, in lanes 64..127 for odd tiles:
     // warps w with (w % 4) / 2 equal to the tile's parity fold it (with 8
@@ -172,6 +175,8 @@ struct GramTC {
     static constexpr int M = 128;                 // A = S: rows 2R..127 are ignored rows of D
     static constexpr int N = RP;                  // B = big
     static constexpr uint32_t IDESC = tc::idesc_tf32(M, N);
+    // M = 64 form: A = S rows 0..63 only; D row r in TMEM lane 32 (r / 16) + r % 16
+    static constexpr uint32_t IDESC64 = tc::idesc_tf32(64, N);
     static constexpr int TCOLS = 2 * N;           // two D buffers (windows alternate)
     static constexpr int SE = 5;                  // entry stages
     static constexpr int ENTB = EW * 4;
@@ -187,8 +192,9 @@ struct GramTC {
     static constexpr int LAST = S_OFF + SB + (VT / 4 - 2) * KGB;
     static constexpr int REACH = LAST + 15 * SBO + KGB + 128;
     static constexpr int BYTES = ((USED > REACH ? USED : REACH) + 127) / 128 * 128;
-    // epilogue buffers alias S0 and S1 once every MMA has completed: bb and sb
-    // sums of even and odd tiles [4][RP][RP + 1], then the b partials [NT][8]
+    // epilogue buffers alias S0 and S1 once every MMA has completed: the bb
+    // and sb sums [2 RP][RP + 1] (the TMA-gather kernel: [4][RP][RP + 1], even
+    // and odd tiles), then the b partials [NT][8]
     static constexpr int TSTR = RP + 1;
     static_assert(VT % 8 == 0 && VT <= NT && (VT * SPV) % NT == 0 && NT % SPV == 0, "tile shape");
     static_assert(FW == 1, "one tile per accumulation window (alternating lane placement)");
@@ -202,7 +208,8 @@ template <int EW, bool BF16, int NOR, int VT, int FW, int NTB>
 __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_gram_tc(ModeArgs a) {
     using G = GramTC<EW, VT, FW, NTB>;
     using RowT = std::conditional_t<BF16, uint2, float4>;   // 4 factor elements
-    constexpr int NT = G::NT, SPV = G::SPV, RS = G::RS, RP = G::RP, ROWB = RP * (BF16 ? 2 : 4), FC = G::FCOLS;
+    constexpr int NT = G::NT, SPV = G::SPV, RS = G::RS, RP = G::RP, ROWB = RP * (BF16 ? 2 : 4);
+    static_assert(NT == 128, "four warps: one 16-row slice of D each");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);   // [2]: MMAs of even / odd tiles
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + 16);
@@ -302,19 +309,24 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
             }
         }
     };
-    // folding warps of tiles of parity fpar: lane block (warp % 4) of D,
-    // columns (warp / 4) FC ..
-    const int fpar = (warp & 3) >> 1;
-    const uint32_t fofs = ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * FC);
-    float acc[FC];
+    // fold: warp w holds D rows 16 w .. 16 w + 15 in its lanes 0-15; thread l
+    // adds row 16 w + l % 16, columns 16 (l / 16) .. + 15 (shape 16x32bx2)
+    const uint32_t fofs = (uint32_t)(32 * warp) << 16;
+    float acc[16];
 #pragma unroll
-    for (int j = 0; j < FC; ++j) acc[j] = 0.f;
+    for (int j = 0; j < 16; ++j) acc[j] = 0.f;
     auto fold = [&](uint32_t taddr) {
-        float v[FC];
-        if constexpr (FC == 32) tc::tmem_ld32(taddr + fofs, v);
-        else tc::tmem_ld16(taddr + fofs, v);
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.16x32bx2.x16.b32 "
+            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16], 16;\n\t"
+            "tcgen05.wait::ld.sync.aligned;\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr + fofs)
+            : "memory");
 #pragma unroll
-        for (int j = 0; j < FC; ++j) acc[j] += v[j];
+        for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(r[j]);
     };
 
     issue_entries(0, pos_of(0));
@@ -354,13 +366,12 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
         if (tid == 0) {
             tc::fence_after();
             const uint32_t buf = s_base + (uint32_t)((t & 1) * G::SB);
-            const uint32_t ashift = (t & 1) ? 8u * G::SBO : 0u;   // odd tiles: S rows -> D lanes 64..127
             const int nks = (tile_n(t) + 7) >> 3;
             for (int ks = 0; ks < nks; ++ks) {
                 const uint32_t kaddr = buf + (uint32_t)(ks * 2 * G::KGB);
-                const uint64_t adesc = tc::smem_desc(kaddr - ashift, G::KGB, G::SBO);
+                const uint64_t adesc = tc::smem_desc(kaddr, G::KGB, G::SBO);
                 const uint64_t bdesc = tc::smem_desc(kaddr, G::KGB, G::SBO);
-                tc::mma_tf32(dbuf(t), adesc, bdesc, G::IDESC, (ks > 0 || t % FW != 0) ? 1u : 0u);
+                tc::mma_tf32(dbuf(t), adesc, bdesc, G::IDESC64, (ks > 0 || t % FW != 0) ? 1u : 0u);
             }
             tc::mma_commit(&mbar[t & 1]);
         }
@@ -369,7 +380,7 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
             // that ended with it is folded
             ok &= tc::mbar_wait(&mbar[(t - 1) & 1], (uint32_t)(((t - 1) >> 1) & 1));
             tc::fence_after();
-            if (t % FW == 0 && fpar == ((t - 1) & 1)) fold(dbuf(t - 1));
+            if (t % FW == 0) fold(dbuf(t - 1));
         }
         if (t + 1 < ntiles) product(ents + ((t + 1) % G::SE) * VT, S + ((t + 1) & 1) * G::SB, tile_n(t + 1));
         if (t + 2 < ntiles) load_rows(ents + ((t + 2) % G::SE) * VT, tile_n(t + 2));
@@ -382,16 +393,17 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
         // the last commit covers every MMA this block issued
         const bool last = tc::mbar_wait(&mbar[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1));
         tc::fence_after();
-        if (ok && last && issued == ntiles && fpar == ((ntiles - 1) & 1)) fold(dbuf(ntiles - 1));
+        if (ok && last && issued == ntiles) fold(dbuf(ntiles - 1));
         ok &= last;
     }
     __syncthreads();   // every MMA has finished: S0 becomes the epilogue buffer
-    float* T4 = reinterpret_cast<float*>(S);          // [warp % 4][RP][TSTR]: bb even, sb even, bb odd, sb odd
-    float* bred = T4 + 4 * RP * G::TSTR;              // [NT][8]
+    float* T2 = reinterpret_cast<float*>(S);          // [2 RP][TSTR]: bb rows, then sb rows
+    float* bred = T2 + 2 * RP * G::TSTR;              // [NT][8]
     {
-        float* T = T4 + (warp & 3) * RP * G::TSTR;
+        const int l = tid & 31;
+        float* T = T2 + (16 * warp + (l & 15)) * G::TSTR + 16 * (l >> 4);
 #pragma unroll
-        for (int j = 0; j < FC; ++j) T[lane * G::TSTR + (warp >> 2) * FC + j] = acc[j];
+        for (int j = 0; j < 16; ++j) T[j] = acc[j];
     }
     reinterpret_cast<float4*>(bred)[2 * tid] = make_float4(bq[0], bq[1], bq[2], bq[3]);
     reinterpret_cast<float4*>(bred)[2 * tid + 1] = make_float4(bq[4], bq[5], bq[6], bq[7]);
@@ -423,8 +435,8 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
             gj = t;
         }
         const int ij = gi * G::TSTR + gj, ji = gj * G::TSTR + gi, L = RP * G::TSTR;
-        const float bb = T4[ij] + T4[2 * L + ij];
-        const float sb = (T4[L + ij] + T4[3 * L + ij]) + (T4[L + ji] + T4[3 * L + ji]);
+        const float bb = T2[ij];
+        const float sb = T2[L + ij] + T2[L + ji];
         out[s] = bb + sb;
     }
     // b[r]: slot-owner threads th = r/8 (mod SPV), in increasing order

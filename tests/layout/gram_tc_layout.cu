@@ -71,10 +71,13 @@ static int check() {
     const int idesc_ok = ((id >> 4) & 3) == 1 && ((id >> 7) & 7) == 2 && ((id >> 10) & 7) == 2 &&
                          ((id >> 15) & 3) == 0 && ((id >> 17) & 63) == (uint32_t)(G::N >> 3) &&
                          ((id >> 24) & 31) == (uint32_t)(G::M >> 4);
+    // the M = 64 form of the split-row kernel: same fields, M / 16 = 4
+    const uint32_t id64 = G::IDESC64;
+    const int idesc64_ok = (id64 & ~(31u << 24)) == (id & ~(31u << 24)) && ((id64 >> 24) & 31) == 4u;
     const int epi = 4 * G::RP * G::TSTR * 4 + NT * 32;
     std::printf("VT %d NT %d bytes %d sb %d kgb %d sbo %d bank_conflicts %d read_lo %ld read_hi %ld rows_ok %d "
-                "desc_ok %d idesc_ok %d epilogue %d tcols %d\n",
-                VT, NT, G::BYTES, G::SB, G::KGB, G::SBO, bad_banks, lo, hi, rows_ok, desc_ok, idesc_ok, epi,
+                "desc_ok %d idesc_ok %d idesc64_ok %d epilogue %d tcols %d\n",
+                VT, NT, G::BYTES, G::SB, G::KGB, G::SBO, bad_banks, lo, hi, rows_ok, desc_ok, idesc_ok, idesc64_ok, epi,
                 G::TCOLS);
     return 0;
 }

@@ -33,7 +33,7 @@ def test_gram_tc_layout(tmp_path):
         f = {tok[i]: int(tok[i + 1]) for i in range(0, len(tok) - 1, 2)}
         assert f["bank_conflicts"] == 0, ln
         assert 0 <= f["read_lo"] and f["read_hi"] <= f["bytes"], ln
-        assert f["rows_ok"] == 1 and f["desc_ok"] == 1 and f["idesc_ok"] == 1, ln
+        assert f["rows_ok"] == 1 and f["desc_ok"] == 1 and f["idesc_ok"] == 1 and f["idesc64_ok"] == 1, ln
         assert f["epilogue"] <= 2 * f["sb"], ln
         # at most 4 resident blocks per SM (registers): their TMEM columns fit the SM's 512
         assert 4 * f["tcols"] <= 512, ln
