@@ -156,7 +156,10 @@ template <int EW, int VT, int FW, int NT_>
 struct GramTC {
     static constexpr int RP = 32;
     static constexpr int NT = NT_;                // threads: 128 or 256
-    static constexpr int BLOCKS = NT == 128 ? 4 : 3;   // resident blocks per SM
+    // resident blocks per SM: five of 128 threads (at most 102 registers; 5 x
+    // (BYTES + 1 KB reserved) = 221 KB of the SM's 228 KB of shared memory;
+    // 5 x 64 TMEM columns of 512)
+    static constexpr int BLOCKS = NT == 128 ? 5 : 3;
     // D's 2R useful rows sit in TMEM lanes 0..63 for even tiles and, with A's
     // descriptor started 8 row groups early, in lanes 64..127 for odd tiles:
     // warps w with (w % 4) / 2 equal to the tile's parity fold it (with 8
@@ -202,6 +205,8 @@ struct GramTC {
     static_assert(4 * RP * TSTR * 4 + NT * 32 <= 2 * SB, "epilogue fits in S0 and S1");
     static_assert(SBO % 16 == 0 && KGB % 16 == 0, "descriptor offsets are 16-byte multiples");
     static_assert(EW == 4, "orders 2-4");
+    static_assert(NT != 128 || BLOCKS * (BYTES + 1024) <= 228 * 1024, "the resident blocks' shared memory fits an SM");
+    static_assert(BLOCKS * TCOLS <= 512, "the resident blocks' tensor memory fits an SM");
 };
 
 template <int EW, bool BF16, int NOR, int VT, int FW, int NTB>

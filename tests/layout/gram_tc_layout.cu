@@ -76,9 +76,9 @@ static int check() {
     const int idesc64_ok = (id64 & ~(31u << 24)) == (id & ~(31u << 24)) && ((id64 >> 24) & 31) == 4u;
     const int epi = 4 * G::RP * G::TSTR * 4 + NT * 32;
     std::printf("VT %d NT %d bytes %d sb %d kgb %d sbo %d bank_conflicts %d read_lo %ld read_hi %ld rows_ok %d "
-                "desc_ok %d idesc_ok %d idesc64_ok %d epilogue %d tcols %d\n",
+                "desc_ok %d idesc_ok %d idesc64_ok %d epilogue %d tcols %d blocks %d\n",
                 VT, NT, G::BYTES, G::SB, G::KGB, G::SBO, bad_banks, lo, hi, rows_ok, desc_ok, idesc_ok, idesc64_ok, epi,
-                G::TCOLS);
+                G::TCOLS, G::BLOCKS);
     return 0;
 }
 

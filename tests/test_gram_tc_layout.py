@@ -35,7 +35,7 @@ def test_gram_tc_layout(tmp_path):
         assert 0 <= f["read_lo"] and f["read_hi"] <= f["bytes"], ln
         assert f["rows_ok"] == 1 and f["desc_ok"] == 1 and f["idesc_ok"] == 1 and f["idesc64_ok"] == 1, ln
         assert f["epilogue"] <= 2 * f["sb"], ln
-        # at most 4 resident blocks per SM (registers): their TMEM columns fit the SM's 512
-        assert 4 * f["tcols"] <= 512, ln
-        # four blocks' shared memory (plus 1 KB reserved each) fit the SM's 228 KB
-        assert 4 * (f["bytes"] + 1024) <= 228 * 1024, ln
+        # the resident blocks of an SM: their TMEM columns fit its 512 and their
+        # shared memory (plus 1 KB reserved each) its 228 KB
+        assert f["blocks"] * f["tcols"] <= 512, ln
+        assert f["blocks"] * (f["bytes"] + 1024) <= 228 * 1024, ln
