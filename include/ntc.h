@@ -81,10 +81,12 @@ ntc_status ntc_create(int order, const int64_t* dims, int rank, double lambda, n
  *                    call instead of allocating and freeing them each time
  *                    (default 1)
  *   "bracket_z"      width, in standard deviations, of the sampler's key bracket
- *                    (default 7; 0 forces the exact fallback selector)
+ *                    (default 6; a row's k-th key falls outside it, so that the
+ *                    row takes the exact fallback selector, with probability
+ *                    about 2e-9 per update; 0 forces the fallback)
  *   "heavy_rows"     rows with more than this many observations are split over
  *                    several thread blocks (default 4096, range 64..4096)
- *   "chunk"          observations per thread block of a split row (default 16384)
+ *   "chunk"          observations per thread block of a split row (default 65536)
  *   "pipeline"       1 (default): split-row sampling runs on its own stream with
  *                    two scratch sets, so the next mode update's sampling runs
  *                    beside this one's Gram (it needs no factors); 0: in stream
