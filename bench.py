@@ -443,8 +443,11 @@ def run_ntc(args):
         "frac": gram_tf / fp32_peak if fp32_peak else None,
         "peak_kind": "measured FP32 FMA microbenchmark, same run", "flops_per_visit": flops_per_visit}}
     if tensor_gram:
-        # issued tensor work: one M=128 x N=R_pad x K=8 TF32 MMA per 8 visits
-        tc_flops_per_visit = 2 * 128 * rp
+        # issued tensor work: one M x N=R_pad x K=8 TF32 MMA per 8 visits, M = 2 R_pad
+        # (the S = [big; small] rows) in the register-gather kernels, M = 128 in the
+        # TMA-gather form
+        m_rows = 128 if args.gram_tc in (2, 3) else 2 * rp
+        tc_flops_per_visit = 2 * m_rows * rp
         tc_tf = gram_visits * tc_flops_per_visit / gram_s / 1e12 if gram_s > 0 else 0.0
         tpk, tpk_kind = tf32_peak()
         compute_roof["roofline_tensor"] = {
