@@ -607,13 +607,15 @@ __device__ __forceinline__ void pair_ab(int T, int p, int* a, int* b) {
     *b = 0;
 }
 
-// Alg. 1 lines 8 and 10-13 for row p, run by warp 0: gradient H y - b
+// Alg. 1 lines 8 and 10-13 for row p, run by one warp: gradient H y - b
 // (= W + Z + lambda y), L_p by the power method (v0 = ones/sqrt(R), fixed
 // iteration count, Rayleigh quotient), projected step, momentum, extrapolation.
-// H is zero outside the leading R x R block, so loops run over RP.
-template <int RP>
-__device__ __forceinline__ void finish_row_warp(const ModeArgs& a, int p, const float* H, const float* bvec,
-                                                float* vsh, int lane) {
+// matvec(x, out) gives this lane's entries (r = lane + 32 t) of H x for x in
+// shared memory (RP floats, 16-byte aligned); H is zero outside the leading
+// R x R block, so loops run over RP.
+template <int RP, class MatVec>
+__device__ __forceinline__ void finish_row_mv(const ModeArgs& a, int p, const float* bvec, float* vsh, int lane,
+                                              const MatVec& matvec) {
     constexpr int PER = RP > 32 ? RP / 32 : 1;
     const int R = a.rank;
     const size_t base = (size_t)a.inv_self[p] * RP;
@@ -626,39 +628,6 @@ __device__ __forceinline__ void finish_row_warp(const ModeArgs& a, int p, const 
         y[t] = in ? (a.read_y ? a.Y[base + r] : al[t]) : 0.f;
         v[t] = in ? (a.vwarm ? a.vwarm[base + r] : 1.0f / sqrtf((float)R)) : 0.f;
     }
-    // for RP <= 32 lane r keeps row r of H in registers; x is read as float4
-    // broadcasts (the sums run over c in the same order either way)
-    float hrow[RP <= 32 ? RP : 1];
-    if constexpr (RP <= 32) {
-#pragma unroll
-        for (int c = 0; c < RP; ++c) hrow[c] = lane < RP ? H[lane * (RP + 1) + c] : 0.f;
-    }
-    auto matvec = [&](const float* x, float* out) {
-        if constexpr (RP <= 32) {
-            float s = 0.f;
-#pragma unroll
-            for (int c = 0; c < RP; c += 4) {
-                const float4 x4 = *reinterpret_cast<const float4*>(x + c);
-                s = fmaf(hrow[c], x4.x, s);
-                s = fmaf(hrow[c + 1], x4.y, s);
-                s = fmaf(hrow[c + 2], x4.z, s);
-                s = fmaf(hrow[c + 3], x4.w, s);
-            }
-            out[0] = s;
-        } else {
-#pragma unroll
-            for (int t = 0; t < PER; ++t) {
-                const int r = lane + 32 * t;
-                float s = 0.f;
-                if (r < RP) {
-                    const float* hr = H + r * (RP + 1);
-#pragma unroll
-                    for (int c = 0; c < RP; ++c) s = fmaf(hr[c], x[c], s);
-                }
-                out[t] = s;
-            }
-        }
-    };
     // gradient: (H y)_r - b_r
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
@@ -725,6 +694,47 @@ __device__ __forceinline__ void finish_row_warp(const ModeArgs& a, int p, const 
             if (a.write_y) a.Y[base + r] = anew + beta * (anew - al[t]);
         }
     }
+}
+
+// The same with H = G + lambda I given in shared memory (stride RP + 1).
+template <int RP>
+__device__ __forceinline__ void finish_row_warp(const ModeArgs& a, int p, const float* H, const float* bvec,
+                                                float* vsh, int lane) {
+    constexpr int PER = RP > 32 ? RP / 32 : 1;
+    // for RP <= 32 lane r keeps row r of H in registers; x is read as float4
+    // broadcasts (the sums run over c in the same order either way)
+    float hrow[RP <= 32 ? RP : 1];
+    if constexpr (RP <= 32) {
+#pragma unroll
+        for (int c = 0; c < RP; ++c) hrow[c] = lane < RP ? H[lane * (RP + 1) + c] : 0.f;
+    }
+    auto matvec = [&](const float* x, float* out) {
+        if constexpr (RP <= 32) {
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < RP; c += 4) {
+                const float4 x4 = *reinterpret_cast<const float4*>(x + c);
+                s = fmaf(hrow[c], x4.x, s);
+                s = fmaf(hrow[c + 1], x4.y, s);
+                s = fmaf(hrow[c + 2], x4.z, s);
+                s = fmaf(hrow[c + 3], x4.w, s);
+            }
+            out[0] = s;
+        } else {
+#pragma unroll
+            for (int t = 0; t < PER; ++t) {
+                const int r = lane + 32 * t;
+                float s = 0.f;
+                if (r < RP) {
+                    const float* hr = H + r * (RP + 1);
+#pragma unroll
+                    for (int c = 0; c < RP; ++c) s = fmaf(hr[c], x[c], s);
+                }
+                out[t] = s;
+            }
+        }
+    };
+    finish_row_mv<RP>(a, p, bvec, vsh, lane, matvec);
 }
 
 // H = G + lambda I for one row, built by one warp: the reduced tiles of the

@@ -4,7 +4,9 @@
 // byte-wise radix select of the k_p-th key (a 256-bin warp histogram per
 // byte), ties taken in position order, the Gram/data sums accumulated in
 // registers, then H, the gradient, L_p and the projected momentum step
-// (finish_row_warp) on the warp's own H in shared memory.  Rating-shaped
+// (finish_row_warp) on the warp's own H in shared memory; at R_pad = 64 and
+// k_p <= 32 the warp keeps the k_p gathered rows K instead and applies H as
+// K^T K + lambda I (finish_row_mv).  Rating-shaped
 // tensors have hundreds of thousands of such rows per mode (users or items
 // with a handful of ratings); a block per row with a 4096-bin histogram select
 // and a reduced-sum round trip through global memory cost them far more than
@@ -165,6 +167,18 @@ __global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArg
         return;
     }
 
+    // K form (R_pad = 64, at most KMAX visits): the visits' k rows go to shared
+    // memory (after the visit list, stride RP + 4) instead of being summed into
+    // G, and the finish evaluates H x = K^T (K x) + lambda x.  For k_p < R_pad
+    // that is less arithmetic and far less shared-memory traffic than forming H
+    // and reading all R_pad^2 entries in each of the power method's matvecs;
+    // the iteration and its result are those of H x (up to rounding order).
+    constexpr bool KFORM = RP == 64;
+    constexpr int KMAX = 32, KST = RP + 4;
+    static_assert(!KFORM || 256 + KMAX * KST <= TS::HA, "K rows fit after the visit list");
+    const bool kform = KFORM && nsel <= KMAX;   // the same in every lane
+    float* Km = H + 256;
+
     // ---- Gram / data sums (Alg. 1 lines 6, 7, 9): lane owns H rows r = lane + 32 t
     // and keeps H[r][(r + d) mod RP] for d = 0 .. RP/2 (each unordered pair once,
     // the pairs at distance RP/2 twice with identical sums)
@@ -203,11 +217,13 @@ __global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArg
                     p = elem(0, i0, r);
                     if (NOR > 1) p *= elem(1, i1, r);
                     if (NOR > 2) p *= elem(2, i2, r);
-                    ksh[r] = p;
+                    if (kform) Km[(vb + v) * KST + r] = p;
+                    else ksh[r] = p;
                 }
                 kk[t] = p;
                 bacc[t] = fmaf(x, p, bacc[t]);
             }
+            if (kform) continue;
             __syncwarp();
 #pragma unroll
             for (int t = 0; t < TS::RPL; ++t) {
@@ -219,6 +235,47 @@ __global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArg
             }
             __syncwarp();
         }
+    }
+    if (kform) {
+#pragma unroll
+        for (int t = 0; t < TS::RPL; ++t) {
+            const int r = lane + 32 * t;
+            if (r < RP) bvec[r] = bacc[t];
+        }
+        __syncwarp();
+        const int R = a.rank;
+        const float lam = a.lambda;
+        auto matvec = [&](const float* x, float* out) {
+            // u_j = K[j] . x in lane j (rows 16-byte aligned; a quarter warp's
+            // row starts fall in distinct banks), then out_r = sum_j K[j][r] u_j
+            float u = 0.f;
+            if (lane < nsel) {
+                const float4* kr = reinterpret_cast<const float4*>(Km + lane * KST);
+                const float4* x4 = reinterpret_cast<const float4*>(x);
+#pragma unroll
+                for (int c = 0; c < RP / 4; ++c) {
+                    const float4 kq = kr[c], xq = x4[c];
+                    u = fmaf(kq.x, xq.x, u);
+                    u = fmaf(kq.y, xq.y, u);
+                    u = fmaf(kq.z, xq.z, u);
+                    u = fmaf(kq.w, xq.w, u);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < TS::RPL; ++t) out[t] = 0.f;
+            for (int j = 0; j < nsel; ++j) {
+                const float uj = __shfl_sync(0xffffffffu, u, j);
+#pragma unroll
+                for (int t = 0; t < TS::RPL; ++t) out[t] = fmaf(Km[j * KST + lane + 32 * t], uj, out[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < TS::RPL; ++t) {
+                const int r = lane + 32 * t;
+                if (r < R) out[t] = fmaf(lam, x[r], out[t]);
+            }
+        };
+        finish_row_mv<RP>(a, row, bvec, vsh, lane, matvec);
+        return;
     }
     // H = G + lambda I (line 9), full symmetric, stride RP + 1; b
 #pragma unroll
