@@ -456,6 +456,30 @@ def run_ntc(args):
             "flops_per_visit_issued": tc_flops_per_visit, "alg_flops_per_visit": flops_per_visit,
             "alg_tflops": gram_tf}
 
+    # split-row sampler: a Philox4x32-10 key for every position of every split row
+    # (more than 4096 observations, the handle's default threshold) in each mode
+    # update, four keys per block; each block takes 16 32x32->64-bit multiplies
+    # (two rounds start from per-thread precomputed values, the rest two per
+    # round), reported against a nominal integer multiply rate of 64 per clock
+    # per SM at the sampled SM clock
+    import math as _m
+    keyed = 0
+    for m in range(N):
+        cnt = np.bincount(p.idx_train[:, m].astype(np.int64), minlength=p.dims[m])
+        keyed += int(cnt[cnt > 4096].sum())
+    keyed_epoch = keyed * _m.ceil(1.0 / p.c - 1e-12)
+    samp_s = prof["heavy_sample"]["ms"] * 1e-3 / max(args.steps, 1)
+    if keyed_epoch and samp_s > 0:
+        mul_s = keyed_epoch / 4 * 16 / samp_s
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mul_peak = 64.0 * nsm * sm_mhz * 1e6
+        compute_roof["sampler"] = {
+            "kernel": "k_heavy_sample", "keys_per_epoch": keyed_epoch, "ms_per_epoch": samp_s * 1e3,
+            "keys_per_s": keyed_epoch / samp_s, "mul64_per_key": 4.0, "int_mul_per_s": mul_s,
+            "int_mul_peak_nominal": mul_peak, "int_mul_frac": mul_s / mul_peak,
+            "note": "event time inside the overlapped epoch; the ncu capture gives the pipe shares"}
+
     # end to end through the C ABI with pinned host buffers
     idx_pin = torch.from_numpy(np.ascontiguousarray(p.idx_train)).pin_memory()
     val_pin = torch.from_numpy(np.ascontiguousarray(p.val_train)).pin_memory()
