@@ -132,25 +132,32 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* kin,
     }
 }
 
-// Keys of `mode` alone (the first pass of the entry sort builds its payloads).
-__global__ void k_extract_mode(const int32_t* idx, int64_t n, int order, int mode, uint32_t* keys) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        keys[e] = (uint32_t)idx[e * order + mode];
+// Keys of `mode` and the 16-byte bucket entries of orders 2-4 in input order,
+// built from the COO in one coalesced pass: the other modes' indices mapped to
+// storage rows (slot w holds mode w, or w + 1 past `mode`), then the value.
+__global__ void k_build_keys_entries(const int32_t* idx, const float* vals, int64_t n, int order, int mode,
+                                     RowMaps maps, uint32_t* keys, uint4* out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t* row = idx + e * order;
+        uint32_t w[3];
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl) {
+            const int src = sl + (sl >= mode ? 1 : 0);
+            w[sl] = src < order ? (uint32_t)maps.inv[src][row[src]] : 0u;
+        }
+        keys[e] = (uint32_t)row[mode];
+        out[e] = make_uint4(w[0], w[1], w[2], __float_as_uint(vals[e]));
+    }
 }
 
 // The same stable scatter with 16-byte bucket entries as payloads, so that
-// the last pass writes the bucket directly.  With FROM_COO (the first pass)
-// a key's entry is built from its COO row: the other modes' indices mapped to
-// storage rows (slot w holds mode w, or w + 1 past `mode`), then the value.
-// Dynamic shared memory: kEntScatterSmem bytes.
+// the last pass writes the bucket directly.  Dynamic shared memory:
+// kEntScatterSmem bytes.
 constexpr size_t kEntScatterSmem = (size_t)(kThreads / 32) * 256 * 4 + (size_t)kSortTile * 4 +
                                    (size_t)kSortTile * 16 + 256 * 4 + (kThreads / 32 + 1) * 4;
-template <bool FROM_COO>
 __global__ void __launch_bounds__(kThreads, 2) k_radix_scatter_ent(const uint32_t* kin, const uint4* pin,
                                                                    uint32_t* kout, uint4* pout, int64_t n, int shift,
-                                                                   const uint32_t* offs, int ntiles, const int32_t* idx,
-                                                                   const float* vals, int order, int mode,
-                                                                   RowMaps maps) {
+                                                                   const uint32_t* offs, int ntiles) {
     extern __shared__ __align__(16) unsigned char es[];
     unsigned(*wh)[256] = reinterpret_cast<unsigned(*)[256]>(es);
     uint32_t* sk = reinterpret_cast<uint32_t*>(es + (kThreads / 32) * 256 * 4);
@@ -211,21 +218,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_radix_scatter_ent(const uint32_
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) {
         const int64_t i = base + r * 32 + lane;
-        if (i < n) {
-            uint4 pay;
-            if constexpr (FROM_COO) {
-                uint32_t w[3];
-#pragma unroll
-                for (int sl = 0; sl < 3; ++sl) {
-                    const int src = sl + (sl >= mode ? 1 : 0);
-                    w[sl] = src < order ? (uint32_t)maps.inv[src][idx[i * order + src]] : 0u;
-                }
-                pay = make_uint4(w[0], w[1], w[2], __float_as_uint(vals[i]));
-            } else {
-                pay = pin[i];
-            }
-            sp[pos[r]] = pay;
-        }
+        if (i < n) sp[pos[r]] = pin[i];
     }
     __syncthreads();
     const int tn = (int)min((int64_t)kSortTile, n - tile0);

@@ -384,13 +384,9 @@ ntc_status sort_mode_entries(ntc_handle* h, int mode, const RowMaps& maps, DevMe
     // once per process (admissions of a server may bucket on several threads)
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = set_smem(k_radix_scatter_ent<true>, kEntScatterSmem);
-        if (attr_err == cudaSuccess) attr_err = set_smem(k_radix_scatter_ent<false>, kEntScatterSmem);
-    });
+    std::call_once(attr_once, [] { attr_err = set_smem(k_radix_scatter_ent, kEntScatterSmem); });
     NTC_CUDA(h, attr_err);
     NTC_CUDA(h, h->entry_tmp.ensure(sizeof(uint4) * (size_t)std::max<int64_t>(n, 1)));
-    k_extract_mode<<<grid_for(n), 256, 0, s>>>(h->coo_idx.as<int32_t>(), n, h->order, mode, k0.as<uint32_t>());
     int bits = 1;
     while (bits < 31 && (1ll << bits) < h->dims[mode]) ++bits;
     const int passes = (bits + 7) / 8;
@@ -400,22 +396,20 @@ ntc_status sort_mode_entries(ntc_handle* h, int mode, const RowMaps& maps, DevMe
     uint32_t *kin = k0.as<uint32_t>(), *kout = k1.as<uint32_t>();
     uint4* bucket = h->bucket[mode].as<uint4>();
     uint4* tmp = h->entry_tmp.as<uint4>();
-    uint4* pin = nullptr;
-    uint4* pout = passes % 2 == 1 ? bucket : tmp;
+    // keys and entries in input order first (coalesced), into the buffer that
+    // leaves the last pass's output in the bucket
+    uint4* pin = passes % 2 == 1 ? tmp : bucket;
+    uint4* pout = pin == bucket ? tmp : bucket;
+    k_build_keys_entries<<<grid_for(n), 256, 0, s>>>(h->coo_idx.as<int32_t>(), h->coo_val.as<float>(), n, h->order, mode,
+                                                     maps, k0.as<uint32_t>(), pin);
     for (int pass = 0; pass < passes && n > 0; ++pass) {
         const int shift = 8 * pass;
         k_radix_hist<<<ntiles, kThreads, 0, s>>>(kin, n, shift, hist.as<uint32_t>(), ntiles);
         k_scan_sums<<<nb, kThreads, 0, s>>>(hist.as<uint32_t>(), nh, sums.as<uint32_t>());
         k_scan_top<<<1, kThreads, 0, s>>>(sums.as<uint32_t>(), nb);
         k_scan_apply<<<nb, kThreads, 0, s>>>(hist.as<uint32_t>(), nh, sums.as<uint32_t>(), hist.as<uint32_t>() + nh);
-        if (pass == 0)
-            k_radix_scatter_ent<true><<<ntiles, kThreads, kEntScatterSmem, s>>>(
-                kin, nullptr, kout, pout, n, shift, hist.as<uint32_t>() + nh, ntiles, h->coo_idx.as<int32_t>(),
-                h->coo_val.as<float>(), h->order, mode, maps);
-        else
-            k_radix_scatter_ent<false><<<ntiles, kThreads, kEntScatterSmem, s>>>(
-                kin, pin, kout, pout, n, shift, hist.as<uint32_t>() + nh, ntiles, nullptr, nullptr, h->order, mode,
-                maps);
+        k_radix_scatter_ent<<<ntiles, kThreads, kEntScatterSmem, s>>>(kin, pin, kout, pout, n, shift,
+                                                                      hist.as<uint32_t>() + nh, ntiles);
         std::swap(kin, kout);
         pin = pout;
         pout = pout == bucket ? tmp : bucket;
