@@ -160,11 +160,9 @@ struct GramTC {
     // (BYTES + 1 KB reserved) = 221 KB of the SM's 228 KB of shared memory;
     // 5 x 64 TMEM columns of 512)
     static constexpr int BLOCKS = NT == 128 ? 5 : 3;
-    // D's 2R useful rows sit in TMEM lanes 0..63 for even tiles and, with A's
-    // descriptor started 8 row groups early, in lanes 64..127 for odd tiles:
-    // warps w with (w % 4) / 2 equal to the tile's parity fold it (with 8
-    // warps, w and w + 4 take 16 columns each), so the folding alternates
-    static constexpr int FCOLS = RP / (NT / 128);
+    // (M = 128 form, TMA-gather kernel: D's 2R useful rows sit in TMEM lanes
+    // 0..63 for even tiles and, with A's descriptor started 8 row groups early,
+    // in lanes 64..127 for odd tiles, so the folding warps alternate)
     static constexpr int SPV = RP / 8;            // product slots per visit: 8 ranks each
     static constexpr int RS = VT * SPV / NT;      // product slots per thread and tile
     static constexpr int SROWS = 2 * RP;          // S rows: big, then small
