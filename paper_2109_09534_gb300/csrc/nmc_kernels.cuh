@@ -871,8 +871,15 @@ __global__ void __launch_bounds__(kLightThreads, 4) k_light(ModeArgs a) {
     auto chosen = [&](int j) -> bool {
         return j < we && (k == n || ((((unsigned long long)keys[j] << 32) | (uq0 + j)) <= T));
     };
+    // one compare pass: the chosen bits of each 32 positions go to a word of
+    // the select's histogram (free now), and the writing pass reads them back
+    unsigned* cmask = hist;
     int wcnt = 0;
-    for (int j0 = wb; j0 < we; j0 += 32) wcnt += __popc(__ballot_sync(0xffffffffu, chosen(j0 + lane)));
+    for (int j0 = wb; j0 < we; j0 += 32) {
+        const unsigned mk = __ballot_sync(0xffffffffu, chosen(j0 + lane));
+        if (lane == 0) cmask[j0 >> 5] = mk;
+        wcnt += __popc(mk);
+    }
     if (lane == 0) scan_tmp[warp] = wcnt;
     __syncthreads();
     int off = 0, nsel = 0;
@@ -882,9 +889,8 @@ __global__ void __launch_bounds__(kLightThreads, 4) k_light(ModeArgs a) {
         nsel += c;
     }
     for (int j0 = wb; j0 < we; j0 += 32) {
-        const bool f = chosen(j0 + lane);
-        const unsigned mk = __ballot_sync(0xffffffffu, f);
-        if (f) vis[off + __popc(mk & ((1u << lane) - 1u))] = (uint16_t)(j0 + lane);
+        const unsigned mk = cmask[j0 >> 5];
+        if ((mk >> lane) & 1u) vis[off + __popc(mk & ((1u << lane) - 1u))] = (uint16_t)(j0 + lane);
         off += __popc(mk);
     }
     __syncthreads();
