@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(NTB, GramTC<EW, VT, FW, NTB>::BLOCKS) k_heavy_
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + 16);
     unsigned char* S = smem_raw + G::S_OFF;
     Entry<EW>* ents = reinterpret_cast<Entry<EW>*>(smem_raw + G::E_OFF);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
 
     const int item = blockIdx.x;
     const uint32_t* list;

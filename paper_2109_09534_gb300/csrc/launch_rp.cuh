@@ -48,6 +48,8 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
         if (e == cudaSuccess) e = set_smem(k_rows_finish<RP>, RowFinish<RP>::bytes());
         if constexpr (EW == 4 && NOR > 0)
             if (e == cudaSuccess) e = set_smem(k_tiny_rows<RP, EW, BF, NOR>, TinyShape<RP>::bytes());
+        if constexpr (EW == 4 && NOR > 0 && RP == 64)
+            if (e == cudaSuccess) e = set_smem(k_tiny_rows<RP, EW, BF, NOR, true>, TinyShape<RP, true>::bytes());
         if constexpr (kTensorGram64<RP, EW, NOR>)
             if (e == cudaSuccess) e = set_smem(k_heavy_gram_tc64<EW, BF, NOR, kTcTile>, GramTC64<EW, kTcTile>::BYTES);
         if constexpr (kTensorGram<RP, EW, NOR>) {
@@ -84,8 +86,28 @@ cudaError_t launch_mode_t(const ModeArgs& a, const ModePlan& p, Launcher& L, boo
                 if constexpr (EW == 4 && NOR > 0) {
                     if (p.n_tiny > 0) {
                         constexpr int W = TinyShape<RP>::WARPS;
-                        k_tiny_rows<RP, EW, BF, NOR><<<(p.n_tiny + W - 1) / W, W * 32, TinyShape<RP>::bytes(), ls>>>(a);
-                        if (p.n_light > 0) ++*L.launches;
+                        // at R_pad 64 the rows of at most kTinyKForm visits (the
+                        // tail: rows are longest first) take the K-only launch
+                        const int nbig = RP == 64 ? p.n_tiny_big : p.n_tiny;
+                        int nl = 0;
+                        if (nbig > 0) {
+                            ModeArgs ab = a;
+                            ab.tiny_end = nbig;
+                            k_tiny_rows<RP, EW, BF, NOR><<<(nbig + W - 1) / W, W * 32, TinyShape<RP>::bytes(), ls>>>(ab);
+                            ++nl;
+                        }
+                        if constexpr (RP == 64) {
+                            if (nbig < p.n_tiny) {
+                                ModeArgs ak = a;
+                                ak.tiny_begin = nbig;
+                                const int nk = p.n_tiny - nbig;
+                                k_tiny_rows<RP, EW, BF, NOR, true>
+                                    <<<(nk + W - 1) / W, W * 32, TinyShape<RP, true>::bytes(), ls>>>(ak);
+                                ++nl;
+                            }
+                        }
+                        // run_on counts one launch
+                        *L.launches += nl - 1 + (p.n_light > 0 ? 1 : 0);
                     }
                 }
                 if (p.n_light > 0)

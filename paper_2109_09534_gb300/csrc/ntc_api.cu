@@ -186,6 +186,8 @@ ntc_status build_plan(ntc_handle* h, int mode, double c) {
     p.rows_skipped = skipped;
     p.n_light = (int)light.size();
     p.n_tiny = (int)tinyv.size();
+    p.n_tiny_big = 0;
+    while (p.n_tiny_big < p.n_tiny && tk[(size_t)p.n_tiny_big] > kTinyKForm) ++p.n_tiny_big;
     p.tiny = tiny;
     p.n_heavy = (int)heavy.size();
     p.n_chunks = (int)chunks.size();
@@ -248,6 +250,8 @@ ModeArgs mode_args(ntc_handle* h, int mode, int inner, uint64_t seed, uint64_t a
     a.tiny_rows = p.tiny_rows.as<int32_t>();
     a.tiny_k = p.tiny_k.as<int32_t>();
     a.n_tiny = p.n_tiny;
+    a.tiny_begin = 0;
+    a.tiny_end = p.n_tiny;
     a.chunks = p.chunks.as<int4>();
     a.chunk_caps = p.chunk_caps.as<int4>();
     a.heavy = p.heavy.as<int4>();

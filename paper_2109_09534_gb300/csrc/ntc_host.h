@@ -51,6 +51,7 @@ struct ModePlan {
     double bracket_z = 0.0;
     int64_t visits = 0, visits_heavy = 0, rows_updated = 0, rows_skipped = 0;
     int n_light = 0, n_heavy = 0, n_chunks = 0, n_tiny = 0;
+    int n_tiny_big = 0;   // leading one-warp rows with more than 32 visits (rows are longest first)
     bool tiny = false;   // rows of <= 509 observations went to the one-warp-per-row kernel
     int64_t cand_total = 0, extra_total = 0;
     int n_groups = 0;

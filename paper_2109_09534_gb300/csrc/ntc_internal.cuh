@@ -15,6 +15,10 @@ constexpr int kReduceGroup = 16;     // split-row partials summed per block of t
 // Largest row handled by one warp from sample to update (tiny_rows.cuh): its
 // positions, widened to whole Philox blocks, are at most 32 lanes x 16 keys.
 constexpr int kTinyMax = 509;
+// One-warp rows at padded rank 64 with at most this many visits keep their
+// gathered rows K instead of forming G, and take a launch of their own with a
+// smaller shared-memory footprint (tiny_rows.cuh).
+constexpr int kTinyKForm = 32;
 
 // Bucket entry of one observation, seen from the mode being updated: the other
 // modes' indices in increasing mode order, then the value in the last word.
@@ -256,6 +260,7 @@ struct ModeArgs {
     const int32_t* tiny_rows;
     const int32_t* tiny_k;
     int n_tiny;
+    int tiny_begin, tiny_end;   // the range of tiny_rows one launch takes
     // heavy rows
     const int4* chunks;       // {heavy index, pos_begin, pos_end, cand_off}
     const int4* chunk_caps;   // {cand_cap, 0, 0, 0}

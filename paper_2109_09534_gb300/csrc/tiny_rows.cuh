@@ -17,22 +17,27 @@
 
 namespace ntc {
 
-template <int RP>
+// KONLY: the launch that takes only rows of at most kTinyKForm visits at
+// R_pad = 64, whose area holds the visit list and K instead of H.
+template <int RP, bool KONLY = false>
 struct TinyShape {
     static constexpr int WARPS = RP > 32 ? 4 : 8;
     static constexpr int RPL = RP > 32 ? 2 : 1;      // H rows owned per lane (rank r = lane + 32 t)
     static constexpr int ND = RP / 2 + 1;            // stored diagonals of each owned row
+    static constexpr int KST = RP + 4;               // K row stride (floats)
     // per warp: H (RP x (RP+1); the visit list, 512 u16, lives there until H
-    // is written, so the area holds at least 256 floats), b, the power-method
-    // vector, k of one visit, and the select's 256-bin histogram
-    static constexpr int HA = RP * (RP + 1) > 256 ? RP * (RP + 1) : 256;
+    // is written, so the area holds at least 256 floats) or, with KONLY, the
+    // visit list then K; b, the power-method vector, k of one visit, and the
+    // select's 256-bin histogram
+    static constexpr int HA = KONLY ? 256 + kTinyKForm * KST : (RP * (RP + 1) > 256 ? RP * (RP + 1) : 256);
     static constexpr int PERW = HA + 3 * RP + 256;
     static constexpr size_t bytes() { return (size_t)WARPS * PERW * 4; }
 };
 
-template <int RP, int EW, bool BF16, int NOR>
+template <int RP, int EW, bool BF16, int NOR, bool KONLY = false>
 __global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArgs a) {
-    using TS = TinyShape<RP>;
+    using TS = TinyShape<RP, KONLY>;
+    static_assert(!KONLY || RP == 64, "the K-only launch is the rank-64 one");
     static_assert(EW == 4 && NOR >= 1 && NOR <= 3, "orders 2-4");
     extern __shared__ __align__(16) float tiny_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -42,8 +47,8 @@ __global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArg
     float* ksh = vsh + RP;
     unsigned* hist = reinterpret_cast<unsigned*>(ksh + RP);
     uint16_t* vis = reinterpret_cast<uint16_t*>(H);
-    const int i = blockIdx.x * TS::WARPS + warp;
-    if (i >= a.n_tiny) return;   // the same in every lane of the warp
+    const int i = a.tiny_begin + blockIdx.x * TS::WARPS + warp;
+    if (i >= a.tiny_end) return;   // the same in every lane of the warp
     const int row = a.tiny_rows[i];
     const int k = a.tiny_k[i];
     const int64_t q0 = a.row_ptr[row];
@@ -174,9 +179,11 @@ __global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArg
     // and reading all R_pad^2 entries in each of the power method's matvecs;
     // the iteration and its result are those of H x (up to rounding order).
     constexpr bool KFORM = RP == 64;
-    constexpr int KMAX = 32, KST = RP + 4;
+    constexpr int KMAX = kTinyKForm, KST = TS::KST;
     static_assert(!KFORM || 256 + KMAX * KST <= TS::HA, "K rows fit after the visit list");
-    const bool kform = KFORM && nsel <= KMAX;   // the same in every lane
+    // the host gives the K-only launch rows of k_p <= kTinyKForm (nsel = k_p)
+    if (KONLY && nsel > KMAX) return;
+    const bool kform = KONLY || (KFORM && nsel <= KMAX);   // the same in every lane
     float* Km = H + 256;
 
     // ---- Gram / data sums (Alg. 1 lines 6, 7, 9): lane owns H rows r = lane + 32 t
@@ -277,25 +284,27 @@ __global__ void __launch_bounds__(TinyShape<RP>::WARPS * 32) k_tiny_rows(ModeArg
         finish_row_mv<RP>(a, row, bvec, vsh, lane, matvec);
         return;
     }
-    // H = G + lambda I (line 9), full symmetric, stride RP + 1; b
+    if constexpr (!KONLY) {
+        // H = G + lambda I (line 9), full symmetric, stride RP + 1; b
 #pragma unroll
-    for (int t = 0; t < TS::RPL; ++t) {
-        const int r = lane + 32 * t;
-        if (r < RP) {
+        for (int t = 0; t < TS::RPL; ++t) {
+            const int r = lane + 32 * t;
+            if (r < RP) {
 #pragma unroll
-            for (int d = 0; d < TS::ND; ++d) {
-                const int c = (r + d) & (RP - 1);
-                H[r * (RP + 1) + c] = acc[t][d];
-                H[c * (RP + 1) + r] = acc[t][d];
+                for (int d = 0; d < TS::ND; ++d) {
+                    const int c = (r + d) & (RP - 1);
+                    H[r * (RP + 1) + c] = acc[t][d];
+                    H[c * (RP + 1) + r] = acc[t][d];
+                }
+                bvec[r] = bacc[t];
             }
-            bvec[r] = bacc[t];
         }
+        __syncwarp();
+        for (int r = lane; r < a.rank; r += 32) H[r * (RP + 1) + r] += a.lambda;
+        __syncwarp();
+        // lines 8, 10-13
+        finish_row_warp<RP>(a, row, H, bvec, vsh, lane);
     }
-    __syncwarp();
-    for (int r = lane; r < a.rank; r += 32) H[r * (RP + 1) + r] += a.lambda;
-    __syncwarp();
-    // lines 8, 10-13
-    finish_row_warp<RP>(a, row, H, bvec, vsh, lane);
 }
 
 }  // namespace ntc

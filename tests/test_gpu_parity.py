@@ -385,8 +385,10 @@ def _tiny_problem(order, rank, seed):
 @pytest.mark.parametrize("order,rank,extra", [
     (3, 8, {}), (3, 16, {}), (3, 32, {}), (3, 64, {}), (3, 5, {}), (2, 24, {}), (4, 40, {}),
     (3, 32, dict(storage_bf16=1)), (3, 20, dict(max_inner=3)), (3, 12, dict(power_warm=1, power_iters=3)),
-    (3, 32, dict(sampler=1))], ids=["r8", "r16", "r32", "r64", "r5", "o2r24", "o4r40", "bf16", "inner3",
-                                    "warm", "perm"])
+    (3, 32, dict(sampler=1)), (3, 64, dict(storage_bf16=1)), (3, 48, dict(power_warm=1, power_iters=3)),
+    (3, 56, dict(max_inner=3))],
+    ids=["r8", "r16", "r32", "r64", "r5", "o2r24", "o4r40", "bf16", "inner3", "warm", "perm", "r64bf16",
+         "r48warm", "r56inner3"])
 def test_tiny_rows_epoch(torch, order, rank, extra):
     """Epoch parity with the one-warp kernel on, and the same epoch through the
     block-per-row kernel (tiny_rows 0): both against the FP64 oracle, and the
