@@ -335,6 +335,23 @@ def test_epoch_permutation_epoch_parity(torch, split):
         assert_factor_close(g.get_factor(m), o.get_factor(m), 1e-5, 1e-4, str(m))
 
 
+@pytest.mark.parametrize("sampler", [0, 1], ids=["independent", "perm"])
+@pytest.mark.parametrize("storage_bf16", [0, 1], ids=["fp32", "bf16"])
+def test_light_rows_rank16_epochs(torch, sampler, storage_bf16):
+    """Every row through the block-per-row kernel at R_pad = 16 (its
+    shuffle-based Gram), both samplers and both storage forms, two epochs
+    against the FP64 oracle."""
+    p = small_zipf(nnz=120_000, dim=600, rank=12, seed=9)
+    g, o = pair(p, torch, gparams=dict(tiny_rows=0, sampler=sampler, storage_bf16=storage_bf16),
+                oparams=dict(sampler=sampler))
+    for e in range(2):
+        g.epoch(0.2, seed=51 + e)
+        o.epoch(0.2, seed=51 + e)
+    tol = (2e-2, 5e-2) if storage_bf16 else (1e-5, 1e-4)
+    for m in range(3):
+        assert_factor_close(g.get_factor(m), o.get_factor(m), *tol, str(m))
+
+
 @pytest.mark.parametrize("overlap", [1, 2])
 def test_light_rows_on_a_side_stream(torch, overlap):
     """overlap 1 / 2: light rows run on a second stream beside the split rows'
