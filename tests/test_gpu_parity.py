@@ -403,9 +403,9 @@ def _tiny_problem(order, rank, seed):
     (3, 8, {}), (3, 16, {}), (3, 32, {}), (3, 64, {}), (3, 5, {}), (2, 24, {}), (4, 40, {}),
     (3, 32, dict(storage_bf16=1)), (3, 20, dict(max_inner=3)), (3, 12, dict(power_warm=1, power_iters=3)),
     (3, 32, dict(sampler=1)), (3, 64, dict(storage_bf16=1)), (3, 48, dict(power_warm=1, power_iters=3)),
-    (3, 56, dict(max_inner=3))],
+    (3, 56, dict(max_inner=3)), (2, 64, {}), (4, 64, dict(sampler=1))],
     ids=["r8", "r16", "r32", "r64", "r5", "o2r24", "o4r40", "bf16", "inner3", "warm", "perm", "r64bf16",
-         "r48warm", "r56inner3"])
+         "r48warm", "r56inner3", "o2r64", "o4r64perm"])
 def test_tiny_rows_epoch(torch, order, rank, extra):
     """Epoch parity with the one-warp kernel on, and the same epoch through the
     block-per-row kernel (tiny_rows 0): both against the FP64 oracle, and the
@@ -426,10 +426,12 @@ def test_tiny_rows_epoch(torch, order, rank, extra):
         g.close()
 
 
-def test_tiny_rows_ties_and_full_rows(torch):
+@pytest.mark.parametrize("rank", [16, 64])
+def test_tiny_rows_ties_and_full_rows(torch, rank):
     """c = 1 (every position of every row) and c = 0.999 (k = n - 1 for rows
-    below 1000 observations): the bisection selects all but the largest key."""
-    p = _tiny_problem(3, 16, seed=5)
+    below 1000 observations): the bisection selects all but the largest key.
+    At rank 64 the rows of at most 32 visits take the K-only launch."""
+    p = _tiny_problem(3, rank, seed=5)
     for c in (1.0, 0.999, 0.5):
         g, o = pair(p, torch, gparams=dict(heavy_rows=1024, chunk=2048))
         g.snmc(1, c, seed=3)
